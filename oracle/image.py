@@ -1,0 +1,83 @@
+"""Image-level driver of the FP64 oracle (test infrastructure only).
+
+For each lost block it builds the extrapolation area L = A u B of Fig. 1:
+an M x M window (M = b + 2d) centred on the b x b loss area B, placed at
+offset (F - M) // 2 of an F x F grid (the DFT period, Section IV uses a 64x64
+FFT for a 48x48 area).  Samples of the window that fall outside the image or
+are marked lost in the mask (any block) are not support: their weight is 0.
+Eq. (3) then gives w on A, Algorithm 1 (``oracle.cfse``) the model g, and
+Re{g} replaces the samples of B (the last loop of Algorithm 1).  Blocks are
+concealed independently of each other from the original mask.
+"""
+from __future__ import annotations
+
+from concurrent.futures import ThreadPoolExecutor
+import os
+
+import numpy as np
+
+from . import cfse, weight
+
+
+def area_inputs(img: np.ndarray, mask: np.ndarray, x: int, y: int, b: int, d: int,
+                F: int, rho: float):
+    """Return (s_grid, w_grid, off): the F x F signal and weight of one block.
+
+    img, mask: 2-D arrays of one image; (x, y) is the top-left sample of the
+    lost block (x = column, y = row).
+    """
+    H, W = img.shape
+    M = b + 2 * d
+    off = (F - M) // 2
+    ys = np.arange(y - d, y - d + M)
+    xs = np.arange(x - d, x - d + M)
+    inside = ((ys >= 0) & (ys < H))[:, None] & ((xs >= 0) & (xs < W))[None, :]
+    yc = np.clip(ys, 0, H - 1)
+    xc = np.clip(xs, 0, W - 1)
+    s_area = img[np.ix_(yc, xc)].astype(np.float64)
+    lost = mask[np.ix_(yc, xc)] != 0
+    support = inside & ~lost
+    w_area = weight(M, M, rho, support.astype(np.uint8))
+    s_grid = np.zeros((F, F))
+    w_grid = np.zeros((F, F))
+    s_grid[off:off + M, off:off + M] = np.where(support, s_area, 0.0)
+    w_grid[off:off + M, off:off + M] = w_area
+    return s_grid, w_grid, off
+
+
+def conceal_block(img, mask, x, y, cls, forced=None):
+    """Run the oracle on one block; returns (patch b x b, CfseResult)."""
+    b, d, F, rho, gamma, iters = (cls["block"], cls["border"], cls["fft"], cls["rho"],
+                                  cls["gamma"], cls["iters"])
+    s_grid, w_grid, off = area_inputs(img, mask, x, y, b, d, F, rho)
+    res = cfse(s_grid, w_grid, gamma, iters, forced=forced)
+    r0 = off + d
+    patch = res.g.real[r0:r0 + b, r0:r0 + b].copy()
+    return patch, res
+
+
+def conceal(images: np.ndarray, mask: np.ndarray, blocks: np.ndarray, classes,
+            forced=None, threads: int | None = None, keep_results: bool = False):
+    """Conceal every block of ``blocks`` (rows: image, x, y, class index).
+
+    images: [N, H, W] (u8 or float); mask: [N, H, W] u8 (1 = lost).
+    classes: list of dicts with keys block, border, fft, rho, gamma, iters.
+    forced: optional list (per block) of forced selection sequences.
+    Returns (patches: list of b x b arrays, results or None).
+    """
+    images = np.asarray(images)
+    mask = np.asarray(mask)
+    blocks = np.asarray(blocks, dtype=np.int64).reshape(-1, 4)
+    nthreads = threads or len(os.sched_getaffinity(0))
+
+    def one(i):
+        im, x, y, c = (int(v) for v in blocks[i])
+        f = None if forced is None else forced[i]
+        return conceal_block(images[im], mask[im], x, y, classes[c], forced=f)
+
+    if len(blocks) == 0:
+        return [], ([] if keep_results else None)
+    with ThreadPoolExecutor(max_workers=nthreads) as ex:
+        out = list(ex.map(one, range(len(blocks))))
+    patches = [p for p, _ in out]
+    return patches, ([r for _, r in out] if keep_results else None)
