@@ -1,0 +1,175 @@
+/*
+ * fse.h -- C ABI of the GB300 (sm_103a) complex-valued Frequency Selective
+ * Extrapolation library (cFSE, Seiler & Kaup, arXiv 2204.14193).
+ *
+ * The library conceals lost b x b blocks of 8-bit or FP32 images.  For every
+ * lost block it builds the extrapolation area L = A u B of Fig. 1 (an
+ * M x M window, M = b + 2d, centred on the loss area B), weights the support
+ * area A with Eq. (3), runs the I iterations of Algorithm 1 in the Fourier
+ * domain on an F x F grid and writes Re{g} on B (the last loop of
+ * Algorithm 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Nothing is thrown across the ABI; every call returns an fse_status.
+ *     fse_last_error() gives a one-line reason for the last failure.
+ *   - Arguments are validated on the host before anything is enqueued; a
+ *     rejected call launches nothing and leaves all outputs untouched.
+ *   - Device-pointer calls are asynchronous on the given CUDA stream (NULL =
+ *     the legacy default stream) and return after enqueueing.  One handle
+ *     serves one stream at a time; calls on one handle must not overlap.
+ *   - Results are deterministic: the same inputs give bit-identical outputs.
+ *   - Image geometry: n_images images of height x width samples.  Image i,
+ *     row y starts at byte (i * height + y) * pitch_bytes of `images`.  The
+ *     loss mask is n_images x height x width bytes, tightly packed (row pitch
+ *     = width).  The output image, when given, is n_images x height x width
+ *     FP32 values, tightly packed; only the samples of B are written.
+ *   - Every sample of a window that lies outside its image, is marked lost in
+ *     the mask (mask != 0), or belongs to the block's own B has weight 0.
+ *     Blocks are concealed independently of each other from the original
+ *     mask (concealed values of one block are never support of another).
+ */
+#ifndef FSE_H
+#define FSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSE_MAX_CLASSES 4
+
+typedef enum {
+    FSE_OK = 0,
+    FSE_ERR_INVALID_ARG = 1, /* a bad argument; nothing was enqueued          */
+    FSE_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. F = 128)       */
+    FSE_ERR_CUDA = 3,        /* a CUDA runtime call failed                     */
+    FSE_ERR_OOM = 4,         /* device or pinned host allocation failed        */
+    FSE_ERR_TIMEOUT = 5,     /* a bounded device wait ran out                  */
+    FSE_ERR_NOT_TRAINED = 6  /* learned initialisation without loaded weights  */
+} fse_status;
+
+typedef enum { FSE_DTYPE_U8 = 0, FSE_DTYPE_F32 = 1 } fse_dtype;
+
+typedef enum {
+    FSE_INIT_ZERO = 0,    /* Algorithm 1 as printed: the model starts at zero */
+    FSE_INIT_LEARNED = 1  /* a CNN estimate e of the area seeds the model     */
+} fse_init_mode;
+
+/* fse_config.flags */
+#define FSE_FLAG_TRACE 1u /* record every selection (see fse_get_trace) */
+
+/*
+ * One block-size class.
+ *   block  b, edge of the lost block (loss area B), 1 <= b <= fft/2
+ *   border d, width of the support frame around B, d >= 1, b + 2d <= fft
+ *   fft    F, FFT size and DFT period: 16, 32 or 64 (Section IV uses 64x64)
+ *   rho    rho-hat of Eq. (3), 0 < rho <= 1
+ *   gamma  orthogonality-deficiency compensation factor of Eq. (9),
+ *          0 < gamma < 2 (the paper uses values in (0, 1])
+ *   iters  I, number of selected basis functions (Algorithm 1), 0 <= I <= 4096
+ */
+typedef struct {
+    int block;
+    int border;
+    int fft;
+    float rho;
+    float gamma;
+    int iters;
+} fse_class;
+
+/*
+ * Handle configuration.
+ *   n_classes   number of valid entries of cls (1..FSE_MAX_CLASSES)
+ *   init        fse_init_mode
+ *   init_iters  iterations run after a learned initialisation (0 = iters)
+ *   device      CUDA device ordinal
+ *   flags       FSE_FLAG_* bits
+ */
+typedef struct {
+    int n_classes;
+    fse_class cls[FSE_MAX_CLASSES];
+    int init;
+    int init_iters;
+    int device;
+    unsigned flags;
+} fse_config;
+
+/* A lost block: image index, top-left sample (x = column, y = row) of B, and
+ * the index of its class in fse_config.cls.  B must lie inside the image. */
+typedef struct {
+    int32_t image;
+    int32_t x;
+    int32_t y;
+    int32_t cls;
+} fse_block;
+
+typedef struct fse_handle fse_handle;
+
+/*
+ * Create a handle on cfg->device: validates the configuration, computes the
+ * Eq. (3) weight tables and the DFT twiddle table on the device, and
+ * allocates the work-queue state.  *out is set only on success.  The handle
+ * owns all its device memory, CUDA graphs and streams.
+ */
+fse_status fse_create(fse_handle **out, const fse_config *cfg);
+
+/*
+ * Conceal a batch of lost blocks (Algorithm 1 once per block), device
+ * buffers.
+ *   images       device, dtype FSE_DTYPE_U8 or FSE_DTYPE_F32, geometry above
+ *   loss_mask    device, uint8, 1 = lost sample, geometry above
+ *   blocks       HOST array of n_blocks descriptors (read during the call)
+ *   out          device FP32 image (geometry above) or NULL; only B samples
+ *                of each block are written
+ *   patches      device FP32 array or NULL: block i's b x b result (row-major)
+ *                at offset sum_{j<i} b_j^2, in the order of `blocks`
+ *   cuda_stream  cudaStream_t to enqueue on
+ * At least one of out, patches must be non-NULL when n_blocks > 0.
+ * n_blocks == 0 is valid and enqueues nothing.  The batch runs as one
+ * persistent, graph-captured launch; the graph is rebuilt only when the block
+ * list or a pointer changes.
+ */
+fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, int n_images,
+                                 int height, int width, size_t pitch_bytes,
+                                 const uint8_t *loss_mask, const fse_block *blocks,
+                                 int n_blocks, float *out, float *patches, void *cuda_stream);
+
+/*
+ * The same computation with HOST buffers (pageable or pinned): copies images
+ * and mask to the handle's device staging buffers, runs the batch, copies the
+ * patches (layout as above) back, and synchronises the stream before it
+ * returns.  `patches` is a host FP32 array of sum_i b_i^2 values.
+ */
+fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dtype,
+                                      int n_images, int height, int width, size_t pitch_bytes,
+                                      const uint8_t *loss_mask, const fse_block *blocks,
+                                      int n_blocks, float *patches, void *cuda_stream);
+
+/*
+ * Copy the selection trace of the last batch (FSE_FLAG_TRACE only) to host
+ * memory, synchronising the handle's last stream first.  For block i (order
+ * of `blocks`) and iteration nu < I of its class, entry i * stride + nu holds
+ *   sel    linear index u * F + v of the selected bin,
+ *   energy |R_w[u,v]|^2 (FP32) at selection,
+ *   coef   c-hat as (re, im).
+ * stride is written to *stride_out (the maximum I over the classes).  Each
+ * output pointer may be NULL (all NULL = query the stride only); cap is the
+ * number of entries each non-NULL array holds and must be >= n_blocks * stride.
+ */
+fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef,
+                         size_t cap, int *stride_out);
+
+/* Reason for the last failure on h (or of fse_create when h is NULL);
+ * never NULL; valid until the next call on h. */
+const char *fse_last_error(const fse_handle *h);
+
+/* Free everything the handle owns (synchronises its streams).  NULL is a no-op. */
+void fse_destroy(fse_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSE_H */

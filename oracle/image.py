@@ -3,8 +3,9 @@
 For each lost block it builds the extrapolation area L = A u B of Fig. 1:
 an M x M window (M = b + 2d) centred on the b x b loss area B, placed at
 offset (F - M) // 2 of an F x F grid (the DFT period, Section IV uses a 64x64
-FFT for a 48x48 area).  Samples of the window that fall outside the image or
-are marked lost in the mask (any block) are not support: their weight is 0.
+FFT for a 48x48 area).  Samples of the window that fall outside the image, are
+marked lost in the mask (any block) or belong to the block's own B are not
+support: their weight is 0.
 Eq. (3) then gives w on A, Algorithm 1 (``oracle.cfse``) the model g, and
 Re{g} replaces the samples of B (the last loop of Algorithm 1).  Blocks are
 concealed independently of each other from the original mask.
@@ -36,7 +37,9 @@ def area_inputs(img: np.ndarray, mask: np.ndarray, x: int, y: int, b: int, d: in
     xc = np.clip(xs, 0, W - 1)
     s_area = img[np.ix_(yc, xc)].astype(np.float64)
     lost = mask[np.ix_(yc, xc)] != 0
-    support = inside & ~lost
+    own_b = np.zeros((M, M), dtype=bool)
+    own_b[d:d + b, d:d + b] = True          # Eq. (3): w = 0 on B
+    support = inside & ~lost & ~own_b
     w_area = weight(M, M, rho, support.astype(np.uint8))
     s_grid = np.zeros((F, F))
     w_grid = np.zeros((F, F))

@@ -1,0 +1,229 @@
+"""GB300 (sm_103a) complex-valued Frequency Selective Extrapolation.
+
+Thin Python binding of the C ABI declared in ``include/fse.h``: the functions
+below carry the C names and only marshal arguments; every step of the
+computation runs in the CUDA kernels of ``libfse.so``.  PyTorch is used for
+device memory and streams only.  There is no CPU fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["fse_class", "fse_config", "fse_block", "FseError", "fse_create", "fse_extrapolate_batch",
+           "fse_extrapolate_batch_host", "fse_get_trace", "fse_last_error", "fse_destroy", "Engine",
+           "library_path", "FSE_DTYPE_U8", "FSE_DTYPE_F32", "FSE_FLAG_TRACE", "FSE_INIT_ZERO",
+           "FSE_INIT_LEARNED"]
+
+FSE_MAX_CLASSES = 4
+FSE_DTYPE_U8, FSE_DTYPE_F32 = 0, 1
+FSE_INIT_ZERO, FSE_INIT_LEARNED = 0, 1
+FSE_FLAG_TRACE = 1
+STATUS = {0: "FSE_OK", 1: "FSE_ERR_INVALID_ARG", 2: "FSE_ERR_UNSUPPORTED", 3: "FSE_ERR_CUDA",
+          4: "FSE_ERR_OOM", 5: "FSE_ERR_TIMEOUT", 6: "FSE_ERR_NOT_TRAINED"}
+
+
+class fse_class(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("fft", ctypes.c_int),
+                ("rho", ctypes.c_float), ("gamma", ctypes.c_float), ("iters", ctypes.c_int)]
+
+
+class fse_config(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int), ("cls", fse_class * FSE_MAX_CLASSES),
+                ("init", ctypes.c_int), ("init_iters", ctypes.c_int), ("device", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
+
+
+class fse_block(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_int32), ("x", ctypes.c_int32), ("y", ctypes.c_int32),
+                ("cls", ctypes.c_int32)]
+
+
+class FseError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if _build.needs_build():
+                _build.build_library()
+            lib = ctypes.CDLL(_build.LIB)
+            vp, c_int, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            lib.fse_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(fse_config)]
+            lib.fse_extrapolate_batch.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp, c_int,
+                                                  vp, vp, vp]
+            lib.fse_extrapolate_batch_host.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp,
+                                                       c_int, vp, vp]
+            lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
+            lib.fse_last_error.argtypes = [vp]
+            lib.fse_last_error.restype = ctypes.c_char_p
+            lib.fse_destroy.argtypes = [vp]
+            lib.fse_destroy.restype = None
+            for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
+                      "fse_get_trace"):
+                getattr(lib, n).restype = c_int
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, h):
+    if status != 0:
+        raise FseError(status, fse_last_error(h))
+
+
+# ------------------------------------------------------------ C-ABI mirror
+def fse_last_error(h) -> str:
+    return _load().fse_last_error(h).decode()
+
+
+def fse_create(cfg: fse_config):
+    """fse_create(): returns an opaque handle (c_void_p)."""
+    h = ctypes.c_void_p()
+    st = _load().fse_create(ctypes.byref(h), ctypes.byref(cfg))
+    _check(st, None)
+    return h
+
+
+def fse_extrapolate_batch(h, images: int, dtype: int, n_images: int, height: int, width: int,
+                          pitch_bytes: int, loss_mask: int, blocks: np.ndarray, n_blocks: int,
+                          out: int | None, patches: int | None, stream: int | None) -> None:
+    """Device-pointer entry point; ``blocks`` is a host int32 [n, 4] array."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+    st = _load().fse_extrapolate_batch(h, images, dtype, n_images, height, width, pitch_bytes,
+                                       loss_mask, blocks.ctypes.data if n_blocks else None, n_blocks,
+                                       out, patches, stream)
+    _check(st, h)
+
+
+def fse_extrapolate_batch_host(h, images: np.ndarray, dtype: int, n_images: int, height: int,
+                               width: int, pitch_bytes: int, loss_mask: np.ndarray,
+                               blocks: np.ndarray, n_blocks: int, patches: np.ndarray,
+                               stream: int | None) -> None:
+    """Host-buffer entry point (numpy arrays, C-contiguous)."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+    st = _load().fse_extrapolate_batch_host(h, images.ctypes.data, dtype, n_images, height, width,
+                                            pitch_bytes, loss_mask.ctypes.data,
+                                            blocks.ctypes.data if n_blocks else None, n_blocks,
+                                            patches.ctypes.data, stream)
+    _check(st, h)
+
+
+def fse_get_trace(h, n_blocks: int):
+    """Returns (sel int32 [n, stride], energy float32 [n, stride], coef complex64 [n, stride])."""
+    stride = ctypes.c_int(0)
+    lib = _load()
+    _check(lib.fse_get_trace(h, None, None, None, 0, ctypes.byref(stride)), h)
+    n = n_blocks * stride.value
+    sel = np.zeros(max(n, 1), np.int32)
+    en = np.zeros(max(n, 1), np.float32)
+    co = np.zeros(2 * max(n, 1), np.float32)
+    _check(lib.fse_get_trace(h, sel.ctypes.data, en.ctypes.data, co.ctypes.data, max(n, 1),
+                             ctypes.byref(stride)), h)
+    s = stride.value
+    return (sel[:n].reshape(n_blocks, s), en[:n].reshape(n_blocks, s),
+            (co[0:2 * n:2] + 1j * co[1:2 * n:2]).astype(np.complex64).reshape(n_blocks, s))
+
+
+def fse_destroy(h) -> None:
+    if h is not None:
+        _load().fse_destroy(h)
+
+
+# --------------------------------------------------------- convenience API
+def make_config(classes, device: int = 0, trace: bool = False) -> fse_config:
+    cfg = fse_config()
+    cfg.n_classes = len(classes)
+    for i, c in enumerate(classes):
+        cfg.cls[i] = fse_class(int(c["block"]), int(c["border"]), int(c["fft"]), float(c["rho"]),
+                               float(c["gamma"]), int(c["iters"]))
+    cfg.init = FSE_INIT_ZERO
+    cfg.init_iters = 0
+    cfg.device = device
+    cfg.flags = FSE_FLAG_TRACE if trace else 0
+    return cfg
+
+
+class Engine:
+    """A handle plus torch-tensor marshalling.
+
+    classes: list of dicts with keys block, border, fft, rho, gamma, iters.
+    """
+
+    def __init__(self, classes, device: int = 0, trace: bool = False):
+        self.classes = [dict(c) for c in classes]
+        self.h = fse_create(make_config(classes, device, trace))
+        self.last_n = 0
+
+    def patch_total(self, blocks) -> int:
+        b = np.array([self.classes[int(c)]["block"] for c in np.asarray(blocks).reshape(-1, 4)[:, 3]])
+        return int(np.sum(b * b)) if b.size else 0
+
+    def run(self, images, mask, blocks, out=None, patches=None, stream=None) -> None:
+        """images: cuda uint8/float32 [N, H, W] (row pitch may exceed W);
+        mask: cuda uint8 [N, H, W] contiguous; blocks: int32 [n, 4]."""
+        import torch
+        assert images.is_cuda and mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
+        N, H, W = images.shape
+        dtype = FSE_DTYPE_U8 if images.dtype == torch.uint8 else FSE_DTYPE_F32
+        if dtype == FSE_DTYPE_F32:
+            assert images.dtype == torch.float32
+        assert images.stride(2) == 1 and (N == 1 or images.stride(0) == H * images.stride(1)), \
+            "images must be [N, H, W] with unit column stride and image stride H * row stride"
+        pitch = images.stride(1) * images.element_size()
+        blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+        if stream is None:
+            stream = torch.cuda.current_stream(images.device).cuda_stream
+        for t in (out, patches):
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        fse_extrapolate_batch(self.h, images.data_ptr(), dtype, N, H, W, pitch, mask.data_ptr(), blocks,
+                              len(blocks), out.data_ptr() if out is not None else None,
+                              patches.data_ptr() if patches is not None else None, stream)
+        self.last_n = len(blocks)
+
+    def run_host(self, images: np.ndarray, mask: np.ndarray, blocks, patches: np.ndarray = None):
+        images = np.ascontiguousarray(images)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        N, H, W = images.shape
+        dtype = FSE_DTYPE_U8 if images.dtype == np.uint8 else FSE_DTYPE_F32
+        if dtype == FSE_DTYPE_F32:
+            images = np.ascontiguousarray(images, dtype=np.float32)
+        blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+        if patches is None:
+            patches = np.zeros(max(self.patch_total(blocks), 1), np.float32)
+        fse_extrapolate_batch_host(self.h, images, dtype, N, H, W, W * images.itemsize, mask, blocks,
+                                   len(blocks), patches, None)
+        self.last_n = len(blocks)
+        return patches
+
+    def trace(self):
+        return fse_get_trace(self.h, self.last_n)
+
+    def close(self):
+        if self.h is not None:
+            fse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

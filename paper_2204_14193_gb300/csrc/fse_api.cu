@@ -1,0 +1,595 @@
+// fse_api.cu -- host runtime behind the C ABI of include/fse.h.
+//
+// Responsibilities: argument validation (nothing is enqueued for a rejected
+// call), the uneven-batch planner (blocks bucketed by class, largest FFT
+// first, grouped into work items of one F=64 / four F=32 / sixteen F=16
+// blocks), the CUDA-graph cache (memset of the work-queue head + one
+// persistent launch, re-captured only when the plan or a pointer changes),
+// the grid-size autotuner, and the host-buffer entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fse.h"
+#include "fse_device.cuh"
+
+using fse::BlockRec;
+using fse::DevParams;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct DeviceGuard {  // restores the caller's current device
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// 64-bit word hash for large arrays (multiply-xorshift per word).
+uint64_t hash_words(const void *data, size_t n, uint64_t h) {
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t w;
+        std::memcpy(&w, p + i, 8);
+        h ^= w + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+        h *= 0xff51afd7ed558ccdull;
+        h ^= h >> 33;
+    }
+    return fnv1a(p + i, n - i, h);
+}
+
+}  // namespace
+
+struct fse_handle {
+    fse_config cfg{};
+    int device = 0;
+    int sm_count = 0;
+    int max_ctas_per_sm = 1;
+    size_t smem_bytes = 0;
+    cudaStream_t cap_stream = nullptr;
+    float *d_wtab[FSE_MAX_CLASSES] = {};
+    float2 *d_tw = nullptr;
+    int *d_counter = nullptr;
+    // block list
+    BlockRec *d_blocks = nullptr;
+    size_t blocks_cap = 0;
+    BlockRec *h_blocks = nullptr;  // pinned staging
+    size_t h_blocks_cap = 0;
+    cudaEvent_t upload_done = nullptr;
+    // trace
+    int *d_tr_sel = nullptr;
+    float *d_tr_energy = nullptr;
+    float2 *d_tr_coef = nullptr;
+    size_t tr_cap = 0;
+    int tr_stride = 0;
+    int last_n_blocks = 0;
+    cudaStream_t last_stream = nullptr;
+    // plan / graph cache
+    uint64_t plan_key = 0;
+    bool graph_valid = false;
+    cudaGraphExec_t gexec = nullptr;
+    DevParams params{};
+    int grid = 0;
+    // autotuner: chosen CTAs per SM, per class-mix signature
+    std::vector<std::pair<uint64_t, int>> tuned;
+    // host-buffer staging
+    void *d_img = nullptr;
+    size_t img_cap = 0;
+    uint8_t *d_mask = nullptr;
+    size_t mask_cap = 0;
+    float *d_patch = nullptr;
+    size_t patch_cap = 0;
+    std::string err = "no error";
+};
+
+namespace {
+
+fse_status fail(fse_handle *h, fse_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+fse_status cuda_fail(fse_handle *h, cudaError_t e, const char *what) {
+    const fse_status st = (e == cudaErrorMemoryAllocation) ? FSE_ERR_OOM : FSE_ERR_CUDA;
+    return fail(h, st, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FSE_CUDA(h, call)                                           \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+    } while (0)
+
+fse_status validate_config(const fse_config *cfg) {
+    if (!cfg) return fail(nullptr, FSE_ERR_INVALID_ARG, "config is NULL");
+    if (cfg->n_classes < 1 || cfg->n_classes > FSE_MAX_CLASSES)
+        return fail(nullptr, FSE_ERR_INVALID_ARG, "n_classes %d not in [1, %d]", cfg->n_classes,
+                    FSE_MAX_CLASSES);
+    for (int i = 0; i < cfg->n_classes; ++i) {
+        const fse_class &c = cfg->cls[i];
+        if (c.fft != 16 && c.fft != 32 && c.fft != 64) {
+            if (c.fft > 0 && (c.fft & (c.fft - 1)) == 0)
+                return fail(nullptr, FSE_ERR_UNSUPPORTED, "class %d: fft %d not supported (16, 32, 64)", i, c.fft);
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: fft %d is not a power of two", i, c.fft);
+        }
+        if (c.block < 1 || 2 * c.block > c.fft)
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: block %d not in [1, fft/2]", i, c.block);
+        if (c.border < 1 || c.block + 2 * c.border > c.fft)
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: border %d needs 1 <= d and b + 2d <= fft", i,
+                        c.border);
+        if (!(c.rho > 0.f && c.rho <= 1.f))
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: rho %g not in (0, 1]", i, (double)c.rho);
+        if (!(c.gamma > 0.f && c.gamma < 2.f))
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: gamma %g not in (0, 2)", i, (double)c.gamma);
+        if (c.iters < 0 || c.iters > 4096)
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: iters %d not in [0, 4096]", i, c.iters);
+    }
+    if (cfg->init != FSE_INIT_ZERO && cfg->init != FSE_INIT_LEARNED)
+        return fail(nullptr, FSE_ERR_INVALID_ARG, "init mode %d unknown", cfg->init);
+    if (cfg->init == FSE_INIT_LEARNED)
+        return fail(nullptr, FSE_ERR_UNSUPPORTED, "learned initialisation is created with fse_create_learned");
+    if (cfg->flags & ~FSE_FLAG_TRACE) return fail(nullptr, FSE_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    return FSE_OK;
+}
+
+// Validation of one batch call; fills the sorted plan on success.
+struct Plan {
+    std::vector<BlockRec> sorted;
+    int n_seg = 0;
+    int seg_cls[FSE_MAX_CLASSES] = {};
+    int seg_item_end[FSE_MAX_CLASSES] = {};
+    int seg_block_start[FSE_MAX_CLASSES] = {};
+    int seg_block_count[FSE_MAX_CLASSES] = {};
+    int total_items = 0;
+    long long patch_total = 0;
+    uint64_t mix_sig = 0;
+};
+
+fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
+                             size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks, Plan &pl) {
+    if (n_blocks < 0) return fail(h, FSE_ERR_INVALID_ARG, "n_blocks %d < 0", n_blocks);
+    if (dtype != FSE_DTYPE_U8 && dtype != FSE_DTYPE_F32) return fail(h, FSE_ERR_INVALID_ARG, "dtype %d unknown", dtype);
+    if (n_blocks == 0) return FSE_OK;
+    if (!images || !mask || !blocks) return fail(h, FSE_ERR_INVALID_ARG, "images, loss_mask and blocks must be non-NULL");
+    if (n_images < 1 || height < 1 || width < 1)
+        return fail(h, FSE_ERR_INVALID_ARG, "bad geometry %d x %d x %d", n_images, height, width);
+    const size_t es = dtype == FSE_DTYPE_U8 ? 1 : 4;
+    if (pitch < (size_t)width * es) return fail(h, FSE_ERR_INVALID_ARG, "pitch %zu < width * %zu", pitch, es);
+    if (dtype == FSE_DTYPE_F32 && (pitch % 4 != 0 || (reinterpret_cast<uintptr_t>(images) & 3)))
+        return fail(h, FSE_ERR_INVALID_ARG, "FP32 images need 4-byte aligned base and pitch");
+    const fse_config &cfg = h->cfg;
+    // class order of the queue: largest F first, then class index
+    int order[FSE_MAX_CLASSES];
+    for (int i = 0; i < cfg.n_classes; ++i) order[i] = i;
+    std::stable_sort(order, order + cfg.n_classes,
+                     [&](int a, int b) { return cfg.cls[a].fft > cfg.cls[b].fft; });
+    std::vector<int> cnt(cfg.n_classes, 0);
+    for (int i = 0; i < n_blocks; ++i) {
+        const fse_block &bk = blocks[i];
+        if (bk.cls < 0 || bk.cls >= cfg.n_classes)
+            return fail(h, FSE_ERR_INVALID_ARG, "block %d: class %d not in [0, %d)", i, bk.cls, cfg.n_classes);
+        const int b = cfg.cls[bk.cls].block;
+        if (bk.image < 0 || bk.image >= n_images || bk.x < 0 || bk.y < 0 || bk.x + b > width || bk.y + b > height)
+            return fail(h, FSE_ERR_INVALID_ARG, "block %d (image %d, x %d, y %d, b %d) is not inside the image", i,
+                        bk.image, bk.x, bk.y, b);
+        cnt[bk.cls]++;
+    }
+    std::vector<long long> poff(n_blocks);
+    long long acc = 0;
+    for (int i = 0; i < n_blocks; ++i) {
+        poff[i] = acc;
+        const int b = cfg.cls[blocks[i].cls].block;
+        acc += (long long)b * b;
+    }
+    pl.patch_total = acc;
+    std::vector<int> start(cfg.n_classes, 0);
+    int pos = 0, items = 0;
+    pl.n_seg = 0;
+    for (int oi = 0; oi < cfg.n_classes; ++oi) {
+        const int c = order[oi];
+        start[c] = pos;
+        if (cnt[c] == 0) continue;
+        const int F = cfg.cls[c].fft;
+        const int bpi = 4096 / (F * F);
+        items += (cnt[c] + bpi - 1) / bpi;
+        pl.seg_cls[pl.n_seg] = c;
+        pl.seg_item_end[pl.n_seg] = items;
+        pl.seg_block_start[pl.n_seg] = pos;
+        pl.seg_block_count[pl.n_seg] = cnt[c];
+        pl.n_seg++;
+        pos += cnt[c];
+    }
+    pl.total_items = items;
+    pl.sorted.resize(n_blocks);
+    std::vector<int> fillp(start);
+    for (int i = 0; i < n_blocks; ++i) {
+        const fse_block &bk = blocks[i];
+        BlockRec r;
+        r.image = bk.image;
+        r.x = bk.x;
+        r.y = bk.y;
+        r.orig = i;
+        r.patch_off = poff[i];
+        r.pad = 0;
+        pl.sorted[fillp[bk.cls]++] = r;
+    }
+    uint64_t sig = 1469598103934665603ull;
+    for (int s = 0; s < pl.n_seg; ++s) {
+        const int c = pl.seg_cls[s];
+        const int bucket = 32 - __builtin_clz((unsigned)pl.seg_block_count[s]);  // log2 size bucket
+        const int key[3] = {c, bucket, cfg.cls[c].iters};
+        sig = fnv1a(key, sizeof key, sig);
+    }
+    pl.mix_sig = sig;
+    return FSE_OK;
+}
+
+template <typename T>
+fse_status grow(fse_handle *h, T **ptr, size_t *cap, size_t need) {
+    if (need <= *cap) return FSE_OK;
+    const size_t n = std::max(need, *cap + *cap / 2);
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(ptr), n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+    *cap = n;
+    return FSE_OK;
+}
+
+fse_status capture_graph(fse_handle *h, int grid, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    FSE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
+    fse::fse_batch_kernel<<<grid, fse::kThreads, h->smem_bytes, h->cap_stream>>>(h->params);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, le, "fse_batch_kernel launch (capture)");
+    }
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+    return FSE_OK;
+}
+
+// Autotuner: time each candidate grid (CTAs per SM) on the actual batch --
+// the outputs are identical for every candidate, so the runs are harmless --
+// and keep the fastest per class-mix signature.
+fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *best_cps) {
+    for (auto &kv : h->tuned)
+        if (kv.first == pl.mix_sig) {
+            *best_cps = kv.second;
+            return FSE_OK;
+        }
+    const int maxc = h->max_ctas_per_sm;
+    int best = maxc;
+    // small batches cannot fill the machine: no measurement needed
+    if ((long long)pl.total_items >= 2LL * h->sm_count && maxc > 1) {
+        cudaEvent_t e0, e1;
+        FSE_CUDA(h, cudaEventCreate(&e0));
+        FSE_CUDA(h, cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (int cps = 1; cps <= maxc; ++cps) {
+            const int grid = std::min(pl.total_items, cps * h->sm_count);
+            cudaGraphExec_t ex = nullptr;
+            fse_status st = capture_graph(h, grid, &ex);
+            if (st != FSE_OK) return st;
+            cudaGraphLaunch(ex, stream);  // warm-up
+            cudaEventRecord(e0, stream);
+            cudaGraphLaunch(ex, stream);
+            cudaEventRecord(e1, stream);
+            cudaError_t se = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaGraphExecDestroy(ex);
+            if (se != cudaSuccess) return cuda_fail(h, se, "autotune run");
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cps;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    h->tuned.emplace_back(pl.mix_sig, best);
+    *best_cps = best;
+    return FSE_OK;
+}
+
+fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
+                     size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks, float *out,
+                     float *patches, cudaStream_t stream) {
+    if (n_blocks < 0) return fail(h, FSE_ERR_INVALID_ARG, "n_blocks %d < 0", n_blocks);
+    if (n_blocks > 0 && !out && !patches) return fail(h, FSE_ERR_INVALID_ARG, "out and patches are both NULL");
+    // plan key: every input of the captured launch (block list, pointers, geometry)
+    uint64_t key = 0;
+    if (n_blocks > 0 && blocks) {
+        key = hash_words(blocks, (size_t)n_blocks * sizeof(fse_block), 0x51ed270b27a1f3c5ull);
+        const uintptr_t ptrs[4] = {(uintptr_t)images, (uintptr_t)mask, (uintptr_t)out, (uintptr_t)patches};
+        const long long geo[6] = {dtype, n_images, height, width, (long long)pitch, n_blocks};
+        key = fnv1a(ptrs, sizeof ptrs, key);
+        key = fnv1a(geo, sizeof geo, key);
+    }
+    if (n_blocks > 0 && h->graph_valid && key == h->plan_key) {
+        // same batch layout as the captured graph: validated when it was planned
+        h->last_n_blocks = n_blocks;
+        h->last_stream = stream;
+        FSE_CUDA(h, cudaGraphLaunch(h->gexec, stream));
+        return FSE_OK;
+    }
+    Plan pl;
+    fse_status st = validate_and_plan(h, images, dtype, n_images, height, width, pitch, mask, blocks, n_blocks, pl);
+    if (st != FSE_OK) return st;
+    h->last_n_blocks = n_blocks;
+    h->last_stream = stream;
+    if (n_blocks == 0) return FSE_OK;
+    const bool trace = (h->cfg.flags & FSE_FLAG_TRACE) != 0;
+    int stride = 0;
+    for (int c = 0; c < h->cfg.n_classes; ++c) stride = std::max(stride, h->cfg.cls[c].iters);
+    stride = std::max(stride, 1);
+
+    if (h->graph_valid) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->graph_valid = false;
+    }
+    // upload the sorted block list through pinned staging
+    if (h->upload_done) cudaEventSynchronize(h->upload_done);
+    if ((size_t)n_blocks > h->h_blocks_cap) {
+        if (h->h_blocks) cudaFreeHost(h->h_blocks);
+        h->h_blocks = nullptr;
+        h->h_blocks_cap = 0;
+        FSE_CUDA(h, cudaMallocHost(&h->h_blocks, (size_t)n_blocks * sizeof(BlockRec)));
+        h->h_blocks_cap = n_blocks;
+    }
+    st = grow(h, &h->d_blocks, &h->blocks_cap, (size_t)n_blocks);
+    if (st != FSE_OK) return st;
+    std::memcpy(h->h_blocks, pl.sorted.data(), (size_t)n_blocks * sizeof(BlockRec));
+    FSE_CUDA(h, cudaMemcpyAsync(h->d_blocks, h->h_blocks, (size_t)n_blocks * sizeof(BlockRec),
+                                cudaMemcpyHostToDevice, stream));
+    FSE_CUDA(h, cudaEventRecord(h->upload_done, stream));
+    if (trace) {
+        const size_t need = (size_t)n_blocks * stride;
+        if (need > h->tr_cap) {
+            cudaFree(h->d_tr_sel);
+            cudaFree(h->d_tr_energy);
+            cudaFree(h->d_tr_coef);
+            h->d_tr_sel = nullptr;
+            h->d_tr_energy = nullptr;
+            h->d_tr_coef = nullptr;
+            h->tr_cap = 0;
+            FSE_CUDA(h, cudaMalloc(&h->d_tr_sel, need * sizeof(int)));
+            FSE_CUDA(h, cudaMalloc(&h->d_tr_energy, need * sizeof(float)));
+            FSE_CUDA(h, cudaMalloc(&h->d_tr_coef, need * sizeof(float2)));
+            h->tr_cap = need;
+        }
+    }
+    h->tr_stride = stride;
+    DevParams &P = h->params;
+    P = DevParams{};
+    P.images = images;
+    P.dtype = dtype;
+    P.H = height;
+    P.W = width;
+    P.pitch = (long long)pitch;
+    P.mask = mask;
+    P.out = out;
+    P.patches = patches;
+    P.blocks = h->d_blocks;
+    P.n_seg = pl.n_seg;
+    for (int sg = 0; sg < pl.n_seg; ++sg) {
+        P.seg_cls[sg] = pl.seg_cls[sg];
+        P.seg_item_end[sg] = pl.seg_item_end[sg];
+        P.seg_block_start[sg] = pl.seg_block_start[sg];
+        P.seg_block_count[sg] = pl.seg_block_count[sg];
+    }
+    P.total_items = pl.total_items;
+    for (int c = 0; c < h->cfg.n_classes; ++c) {
+        const fse_class &k = h->cfg.cls[c];
+        fse::DevClass &D = P.cls[c];
+        D.F = k.fft;
+        D.b = k.block;
+        D.d = k.border;
+        D.M = k.block + 2 * k.border;
+        D.off = (k.fft - D.M) / 2;
+        D.iters = k.iters;
+        D.bpi = 4096 / (k.fft * k.fft);
+        D.gamma = k.gamma;
+        D.wtab = h->d_wtab[c];
+    }
+    P.counter = h->d_counter;
+    P.tr_sel = trace ? h->d_tr_sel : nullptr;
+    P.tr_energy = trace ? h->d_tr_energy : nullptr;
+    P.tr_coef = trace ? h->d_tr_coef : nullptr;
+    P.tr_stride = stride;
+    P.tw = h->d_tw;
+    int cps = h->max_ctas_per_sm;
+    st = autotune(h, pl, stream, &cps);
+    if (st != FSE_OK) return st;
+    h->grid = std::max(1, std::min(pl.total_items, cps * h->sm_count));
+    st = capture_graph(h, h->grid, &h->gexec);
+    if (st != FSE_OK) return st;
+    h->graph_valid = true;
+    h->plan_key = key;
+    FSE_CUDA(h, cudaGraphLaunch(h->gexec, stream));
+    return FSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fse_status fse_create(fse_handle **out, const fse_config *cfg) {
+    if (!out) return fail(nullptr, FSE_ERR_INVALID_ARG, "out is NULL");
+    fse_status st = validate_config(cfg);
+    if (st != FSE_OK) return st;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(nullptr, FSE_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    if (cfg->device < 0 || cfg->device >= ndev)
+        return fail(nullptr, FSE_ERR_INVALID_ARG, "device %d not in [0, %d)", cfg->device, ndev);
+    DeviceGuard guard(cfg->device);
+    fse_handle *h = new fse_handle();
+    h->cfg = *cfg;
+    h->device = cfg->device;
+    auto bail = [&](fse_status s) {
+        g_create_error = h->err;
+        fse_destroy(h);
+        return s;
+    };
+#define CREATE_CUDA(call)                                    \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call)); \
+    } while (0)
+    cudaDeviceProp prop;
+    CREATE_CUDA(cudaGetDeviceProperties(&prop, h->device));
+    h->sm_count = prop.multiProcessorCount;
+    // dynamic smem: the largest per-item region over the configured classes
+    size_t smem = 0;
+    for (int c = 0; c < cfg->n_classes; ++c) {
+        const int F = cfg->cls[c].fft;
+        smem = std::max(smem, (size_t)(4096 / (F * F)) * 16 * F * F);
+    }
+    h->smem_bytes = smem;
+    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel, fse::kThreads, smem));
+    if (occ < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
+    h->max_ctas_per_sm = occ;
+    CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CREATE_CUDA(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming));
+    CREATE_CUDA(cudaMalloc(&h->d_counter, sizeof(int)));
+    CREATE_CUDA(cudaMalloc(&h->d_tw, 64 * sizeof(float2)));
+    fse::twiddle_kernel<<<1, 64, 0, h->cap_stream>>>(h->d_tw);
+    CREATE_CUDA(cudaGetLastError());
+    for (int c = 0; c < cfg->n_classes; ++c) {
+        const int M = cfg->cls[c].block + 2 * cfg->cls[c].border;
+        CREATE_CUDA(cudaMalloc(&h->d_wtab[c], (size_t)M * M * sizeof(float)));
+        fse::weight_table_kernel<<<(M * M + 255) / 256, 256, 0, h->cap_stream>>>(h->d_wtab[c], M,
+                                                                                (double)cfg->cls[c].rho);
+        CREATE_CUDA(cudaGetLastError());
+    }
+    CREATE_CUDA(cudaStreamSynchronize(h->cap_stream));
+#undef CREATE_CUDA
+    *out = h;
+    return FSE_OK;
+}
+
+fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
+                                 size_t pitch_bytes, const uint8_t *loss_mask, const fse_block *blocks, int n_blocks,
+                                 float *out, float *patches, void *cuda_stream) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard guard(h->device);
+    return run_batch(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks, n_blocks, out,
+                     patches, static_cast<cudaStream_t>(cuda_stream));
+}
+
+fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dtype, int n_images, int height,
+                                      int width, size_t pitch_bytes, const uint8_t *loss_mask,
+                                      const fse_block *blocks, int n_blocks, float *patches, void *cuda_stream) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard guard(h->device);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (n_blocks < 0) return fail(h, FSE_ERR_INVALID_ARG, "n_blocks %d < 0", n_blocks);
+    if (n_blocks == 0) {
+        h->last_n_blocks = 0;
+        return FSE_OK;
+    }
+    if (!patches) return fail(h, FSE_ERR_INVALID_ARG, "patches is NULL");
+    // validate before any copy (the geometry is checked again by run_batch)
+    Plan pl;
+    fse_status st = validate_and_plan(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks,
+                                      n_blocks, pl);
+    if (st != FSE_OK) return st;
+    const size_t img_bytes = (size_t)n_images * height * pitch_bytes;
+    const size_t mask_bytes = (size_t)n_images * height * width;
+    st = grow(h, reinterpret_cast<unsigned char **>(&h->d_img), &h->img_cap, img_bytes);
+    if (st != FSE_OK) return st;
+    st = grow(h, &h->d_mask, &h->mask_cap, mask_bytes);
+    if (st != FSE_OK) return st;
+    st = grow(h, &h->d_patch, &h->patch_cap, (size_t)pl.patch_total);
+    if (st != FSE_OK) return st;
+    FSE_CUDA(h, cudaMemcpyAsync(h->d_img, images, img_bytes, cudaMemcpyHostToDevice, stream));
+    FSE_CUDA(h, cudaMemcpyAsync(h->d_mask, loss_mask, mask_bytes, cudaMemcpyHostToDevice, stream));
+    st = run_batch(h, h->d_img, dtype, n_images, height, width, pitch_bytes, h->d_mask, blocks, n_blocks, nullptr,
+                   h->d_patch, stream);
+    if (st != FSE_OK) return st;
+    FSE_CUDA(h, cudaMemcpyAsync(patches, h->d_patch, (size_t)pl.patch_total * sizeof(float), cudaMemcpyDeviceToHost,
+                                stream));
+    FSE_CUDA(h, cudaStreamSynchronize(stream));
+    return FSE_OK;
+}
+
+fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef, size_t cap, int *stride_out) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (!(h->cfg.flags & FSE_FLAG_TRACE)) return fail(h, FSE_ERR_INVALID_ARG, "handle was created without FSE_FLAG_TRACE");
+    DeviceGuard guard(h->device);
+    const size_t n = (size_t)h->last_n_blocks * h->tr_stride;
+    if (stride_out) *stride_out = h->tr_stride;
+    if (n == 0 || (!sel && !energy && !coef)) return FSE_OK;   // stride query
+    if (cap < n) return fail(h, FSE_ERR_INVALID_ARG, "cap %zu < n_blocks * stride = %zu", cap, n);
+    FSE_CUDA(h, cudaStreamSynchronize(h->last_stream));
+    if (sel) FSE_CUDA(h, cudaMemcpy(sel, h->d_tr_sel, n * sizeof(int), cudaMemcpyDeviceToHost));
+    if (energy) FSE_CUDA(h, cudaMemcpy(energy, h->d_tr_energy, n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (coef) FSE_CUDA(h, cudaMemcpy(coef, h->d_tr_coef, n * sizeof(float2), cudaMemcpyDeviceToHost));
+    return FSE_OK;
+}
+
+const char *fse_last_error(const fse_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void fse_destroy(fse_handle *h) {
+    if (!h) return;
+    {
+        DeviceGuard guard(h->device);
+        if (h->last_stream || h->cap_stream) cudaDeviceSynchronize();
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        for (auto &p : h->d_wtab) cudaFree(p);
+        cudaFree(h->d_tw);
+        cudaFree(h->d_counter);
+        cudaFree(h->d_blocks);
+        if (h->h_blocks) cudaFreeHost(h->h_blocks);
+        cudaFree(h->d_tr_sel);
+        cudaFree(h->d_tr_energy);
+        cudaFree(h->d_tr_coef);
+        cudaFree(h->d_img);
+        cudaFree(h->d_mask);
+        cudaFree(h->d_patch);
+        if (h->upload_done) cudaEventDestroy(h->upload_done);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -53,6 +53,40 @@ def _render(p, H: int, W: int, frame: int, rng: np.random.Generator, u8: bool) -
     return img.astype(np.float32)
 
 
+def _render_torch(p, H: int, W: int, frames: int, seed: int, u8: bool, device):
+    """The same content model evaluated with torch on ``device`` (used for
+    large benchmark batches).  Only the noise realisation differs from the
+    numpy path (torch's generator on that device, seeded with ``seed``)."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    x = torch.arange(W, dtype=torch.float64, device=dev)
+    y = torch.arange(H, dtype=torch.float64, device=dev)
+    out = torch.empty((frames, H, W), dtype=torch.uint8 if u8 else torch.float32, device=dev)
+    proj = (y[:, None] * np.sin(p["theta"]) + x[None, :] * np.cos(p["theta"])).float()
+    for t in range(frames):
+        img = torch.full((H, W), 128.0, dtype=torch.float32, device=dev)
+        for i in range(8):
+            ph = float(p["phi"][i] + p["omega"][i] * t)
+            ax = 2.0 * np.pi * float(p["fx"][i]) * x + ph
+            ay = 2.0 * np.pi * float(p["fy"][i]) * y
+            img += float(p["a"][i]) * (torch.outer(torch.cos(ay), torch.cos(ax))
+                                       - torch.outer(torch.sin(ay), torch.sin(ax))).float()
+        img += float(p["h"]) * (proj > float(p["t"] + p["drift"] * t)).float()
+        img += 2.0 * torch.randn((H, W), generator=gen, device=dev, dtype=torch.float32)
+        img.clamp_(0.0, 255.0)
+        out[t] = torch.round(img).to(torch.uint8) if u8 else img
+    return out
+
+
+def make_video_torch(seed: int, frames: int, H: int, W: int, u8: bool = True, device="cuda"):
+    """make_video rendered with torch on ``device`` (a torch tensor)."""
+    rng = np.random.default_rng(seed)
+    p = _params(rng, H, W)
+    return _render_torch(p, H, W, frames, seed, u8, device)
+
+
 def make_image(seed: int, H: int, W: int, u8: bool = True) -> np.ndarray:
     """One synthetic image [H, W] (uint8 or float32)."""
     rng = np.random.default_rng(seed)

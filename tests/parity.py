@@ -1,0 +1,124 @@
+"""Parity harness: the CUDA path against the FP64 oracle.
+
+Readings used (also in the design notes):
+  - selections are compared modulo the global conjugate mirror
+    (u, v) -> (-u, -v) mod F: for real input the two choices give the same
+    Re{g} (the mirrored trajectory has R' = conj(R[-k]) and g' = conj(g));
+  - every GPU pick must be an epsilon-argmax of the oracle's FP64 residual
+    along the same selection sequence: |R_w[pick]|^2 >= (1 - eps) max |R_w|^2
+    with eps = EPS_TIE + ROUND_K * delta, where delta = |e32 - e64| / e64 is
+    the relative deviation of the kernel's own FP32 energy of that pick from
+    its FP64 value.  The argmax is decided in the kernel's precision: late in
+    the iteration, when the residual has fallen far below the initial
+    spectrum, FP32 cannot order energies closer than a few delta, and such a
+    pick is a tie at that precision.  delta itself must stay below
+    DELTA_MAX, so a wrong residual cannot hide behind a widened band;
+  - pixels are compared with the oracle replayed along the GPU's selection
+    sequence (guided replay), |GPU - oracle| <= PIX_TOL on the 0-255 scale.
+"""
+from __future__ import annotations
+
+from concurrent.futures import ThreadPoolExecutor
+import os
+
+import numpy as np
+
+import oracle
+from oracle import image as oimage
+
+EPS_TIE = 1e-5      # near-tie band of the top-two energies (relative)
+ROUND_K = 4.0       # band widening per unit of measured FP32 energy deviation
+DELTA_MAX = 2e-4    # largest FP32 energy deviation accepted at any pick
+PIX_TOL = 1e-2      # absolute pixel tolerance, 0-255 scale
+
+
+def mirror(sel, F):
+    sel = np.asarray(sel, dtype=np.int64)
+    return ((-(sel // F)) % F) * F + ((-(sel % F)) % F)
+
+
+def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None):
+    """Compare one block.  Returns a dict of diagnostics; raises nothing.
+    gpu_sel / gpu_energy: the kernel's selection trace and FP32 energies."""
+    im, x, y, c = (int(v) for v in blk)
+    k = cls[c]
+    F, b, I = k["fft"], k["block"], k["iters"]
+    s_grid, w_grid, off = oimage.area_inputs(img, mask, x, y, b, k["border"], F, k["rho"])
+    out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False,
+               max_delta=0.0, widened=False)
+    free = oracle.cfse(s_grid, w_grid, k["gamma"], I)
+    r0 = off + k["border"]
+    free_patch = free.g.real[r0:r0 + b, r0:r0 + b]
+    if gpu_sel is None:
+        # no trace: only the free run can be compared
+        out["max_pix"] = float(np.max(np.abs(free_patch - gpu_patch))) if I else float(np.max(np.abs(gpu_patch)))
+        out["ok"] = out["max_pix"] <= PIX_TOL
+        return out
+    gsel = np.asarray(gpu_sel[:I], dtype=np.int64)
+    if I:
+        same = gsel == free.sel
+        mir = gsel == mirror(free.sel, F)
+        if same.all():
+            pass
+        elif mir.all():
+            out["mirror"] = True
+        else:
+            # first index where neither the direct nor the mirrored sequence matches
+            a = int(np.argmin(same)) if not same.all() else I
+            bq = int(np.argmin(mir)) if not mir.all() else I
+            out["first_div"] = max(a, bq)
+    guided = oracle.cfse(s_grid, w_grid, k["gamma"], I, forced=gsel.astype(np.int32))
+    if I:
+        ratio = guided.e_sel / np.maximum(guided.e_max, 1e-300)
+        ratio[guided.e_max == 0] = 1.0
+        out["worst_ratio"] = float(ratio.min())
+        if gpu_energy is not None:
+            e32 = np.asarray(gpu_energy[:I], dtype=np.float64)
+            delta = np.abs(e32 - guided.e_sel) / np.maximum(guided.e_sel, 1e-300)
+            delta[guided.e_sel == 0] = 0.0
+        else:
+            delta = np.zeros(I)
+        out["max_delta"] = float(delta.max())
+        band = EPS_TIE + ROUND_K * delta
+        if np.any(1.0 - ratio > band) or out["max_delta"] > DELTA_MAX:
+            out["ok"] = False
+        out["widened"] = bool(np.any(1.0 - ratio > EPS_TIE))
+    gp = guided.g.real[r0:r0 + b, r0:r0 + b]
+    out["max_pix"] = float(np.max(np.abs(gp - gpu_patch)))
+    if out["max_pix"] > PIX_TOL:
+        out["ok"] = False
+    return out
+
+
+def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None):
+    """Check every block of a batch; patches is the flat patch array (caller
+    order), sels / energies the [n, stride] trace or None."""
+    blocks = np.asarray(blocks).reshape(-1, 4)
+    offs = np.zeros(len(blocks) + 1, np.int64)
+    for i, bk in enumerate(blocks):
+        b = cls[int(bk[3])]["block"]
+        offs[i + 1] = offs[i] + b * b
+
+    def one(i):
+        bk = blocks[i]
+        b = cls[int(bk[3])]["block"]
+        p = np.asarray(patches[offs[i]:offs[i + 1]], dtype=np.float64).reshape(b, b)
+        return check_block(images[int(bk[0])], mask[int(bk[0])], bk, cls, p,
+                           None if sels is None else sels[i],
+                           None if energies is None else energies[i])
+
+    n = threads or len(os.sched_getaffinity(0))
+    with ThreadPoolExecutor(max_workers=n) as ex:
+        return list(ex.map(one, range(len(blocks))))
+
+
+def summarize(results):
+    ok = all(r["ok"] for r in results)
+    worst_pix = max((r["max_pix"] for r in results), default=0.0)
+    worst_ratio = min((r["worst_ratio"] for r in results), default=1.0)
+    n_div = sum(r["first_div"] is not None for r in results)
+    n_mir = sum(r["mirror"] for r in results)
+    n_wid = sum(r["widened"] for r in results)
+    max_delta = max((r["max_delta"] for r in results), default=0.0)
+    return dict(ok=ok, n=len(results), worst_pix=worst_pix, worst_ratio=worst_ratio,
+                diverged=n_div, mirrored=n_mir, widened=n_wid, max_delta=max_delta)

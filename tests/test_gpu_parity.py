@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every test here needs a GB300; inputs are seeded synthetic images of the
+shapes the paper's experiment uses (Section IV: 16x16 losses, 16-sample
+support border, 64x64 FFT, rho 0.8).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import image as oimage
+from paper_2204_14193_gb300 import synth
+import parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+C64 = dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=200)
+C32 = dict(block=8, border=12, fft=32, rho=0.8, gamma=0.5, iters=200)
+C16 = dict(block=4, border=6, fft=16, rho=0.8, gamma=0.5, iters=200)
+
+
+@pytest.fixture(scope="module")
+def fse():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2204_14193_gb300 as P
+    return P
+
+
+def run_gpu(P, classes, images, mask, blocks, trace=True, out_image=False):
+    eng = P.Engine(classes, trace=trace)
+    dimg = torch.from_numpy(np.ascontiguousarray(images)).cuda()
+    dmask = torch.from_numpy(np.ascontiguousarray(mask)).cuda()
+    n = eng.patch_total(blocks)
+    patches = torch.zeros(max(n, 1), dtype=torch.float32, device="cuda")
+    out = torch.zeros(images.shape, dtype=torch.float32, device="cuda") if out_image else None
+    eng.run(dimg, dmask, blocks, out=out, patches=patches)
+    torch.cuda.synchronize()
+    sel = eng.trace()[:2] if trace else None
+    res = (patches.cpu().numpy()[:n], sel, out.cpu().numpy() if out_image else None)
+    eng.close()
+    return res
+
+
+def assert_parity(images, mask, blocks, classes, patches, trace):
+    res = parity.check_batch(images, mask, blocks, classes, patches, trace[0], trace[1])
+    s = parity.summarize(res)
+    print("parity:", s)
+    assert s["ok"], s
+    return s
+
+
+# ---------------------------------------------------------------- configs
+def test_single_area_fp32_i100(fse):
+    """One 48x48 FP32 area, 16x16 hole centred, F=64, I=100."""
+    img = synth.make_image(1, 48, 48, u8=False)[None]
+    blocks = np.array([[0, 16, 16, 0]], np.int32)
+    mask = synth.loss_mask(blocks, [16], 1, 48, 48)
+    cls = [dict(C64, iters=100)]
+    patches, sel, _ = run_gpu(fse, cls, img, mask, blocks)
+    s = assert_parity(img, mask, blocks, cls, patches, sel)
+    assert s["worst_pix"] <= parity.PIX_TOL
+
+
+def test_512_u8_256_blocks_i200(fse):
+    """512x512 8-bit image, 25% of 16x16 blocks lost (non-adjacent), I=200."""
+    img = synth.make_image(2, 512, 512)[None]
+    blocks = synth.grid_losses(3, 512, 512, 16, 0.25, non_adjacent=True)
+    assert len(blocks) == 256
+    mask = synth.loss_mask(blocks, [16], 1, 512, 512)
+    patches, sel, out = run_gpu(fse, [C64], img, mask, blocks, out_image=True)
+    assert_parity(img, mask, blocks, [C64], patches, sel)
+    # the image output holds the same values at the lost samples
+    for i, (_, x, y, _c) in enumerate(blocks[:16]):
+        np.testing.assert_array_equal(out[0, y:y + 16, x:x + 16].ravel(), patches[256 * i:256 * (i + 1)])
+
+
+def test_uneven_video_two_frames(fse):
+    """Mixed 4/8/16 losses (FFT 16/32/64) of two 1080p frames in one launch."""
+    vid = synth.make_video(4, 2, 1080, 1920)
+    blocks = np.concatenate([synth.uneven_losses(10 + t, 1080, 1920, image=t) for t in range(2)])
+    cls = [C16, C32, C64]
+    mask = synth.loss_mask(blocks, [4, 8, 16], 2, 1080, 1920)
+    patches, sel, _ = run_gpu(fse, cls, vid, mask, blocks)
+    assert_parity(vid, mask, blocks, cls, patches, sel)
+
+
+# ------------------------------------------------------------- edge cases
+def test_iteration_counts_0_1_2(fse):
+    img = synth.make_image(5, 128, 128)[None]
+    blocks = synth.grid_losses(6, 128, 128, 16, 0.2, non_adjacent=True)
+    mask = synth.loss_mask(blocks, [16], 1, 128, 128)
+    for I in (0, 1, 2):
+        cls = [dict(C64, iters=I)]
+        patches, sel, _ = run_gpu(fse, cls, img, mask, blocks)
+        if I == 0:
+            assert np.all(patches == 0)
+        else:
+            assert_parity(img, mask, blocks, cls, patches, sel)
+
+
+def test_border_blocks_and_diagonal_neighbours(fse):
+    """Supports reaching past every image edge, lost diagonal neighbours."""
+    H, W = 96, 80
+    img = synth.make_image(7, H, W)[None]
+    blocks = np.array([[0, 0, 0, 0], [0, 16, 16, 0], [0, 64, 0, 0], [0, 0, 80, 0],
+                       [0, 64, 80, 0], [0, 32, 48, 0], [0, 48, 32, 0]], np.int32)
+    mask = synth.loss_mask(blocks, [16], 1, H, W)
+    patches, sel, _ = run_gpu(fse, [C64], img, mask, blocks)
+    assert_parity(img, mask, blocks, [C64], patches, sel)
+
+
+def test_small_fft_tails_and_max_block(fse):
+    """F=16 / F=32 items that are not full (tails) and the largest block
+    (b = F/2) of each size."""
+    H, W = 200, 232
+    img = synth.make_image(8, H, W)[None]
+    cls = [dict(C16, iters=50), dict(C32, iters=50), dict(block=8, border=4, fft=16, rho=0.8, gamma=0.5, iters=40),
+           dict(block=32, border=16, fft=64, rho=0.8, gamma=0.5, iters=30)]
+    rows = []
+    rng = np.random.default_rng(9)
+    occ = np.zeros((H, W), bool)
+    for c, n in ((0, 19), (1, 7), (2, 5), (3, 2)):
+        b = cls[c]["block"]
+        placed = 0
+        while placed < n:
+            y = int(rng.integers(0, H - b + 1))
+            x = int(rng.integers(0, W - b + 1))
+            if occ[y:y + b, x:x + b].any():
+                continue
+            occ[y:y + b, x:x + b] = True
+            rows.append((0, x, y, c))
+            placed += 1
+    blocks = np.array(rows, np.int32)
+    mask = synth.loss_mask(blocks, [c["block"] for c in cls], 1, H, W)
+    patches, sel, _ = run_gpu(fse, cls, img, mask, blocks)
+    assert_parity(img, mask, blocks, cls, patches, sel)
+
+
+def test_rho_one_and_gamma_variants(fse):
+    img = synth.make_image(11, 128, 128)[None]
+    blocks = synth.grid_losses(12, 128, 128, 16, 0.15, non_adjacent=True)
+    mask = synth.loss_mask(blocks, [16], 1, 128, 128)
+    for rho, gamma in ((1.0, 0.5), (0.8, 0.2), (0.9, 1.0)):
+        cls = [dict(C64, rho=rho, gamma=gamma, iters=80)]
+        patches, sel, _ = run_gpu(fse, cls, img, mask, blocks)
+        assert_parity(img, mask, blocks, cls, patches, sel)
+
+
+def test_golden_closed_forms_through_abi(fse):
+    """tests/golden: constant support -> c (1 - (1-gamma)^I); a single real
+    basis function (-1)^(x+y) is recovered in one iteration with gamma = 1."""
+    H = W = 64
+    blocks = np.array([[0, 16, 16, 0], [0, 32, 32, 0]], np.int32)
+    mask = synth.loss_mask(blocks, [16], 1, H, W)
+    const = np.full((1, H, W), 100.0, np.float32)
+    for gamma, I, expect in ((0.5, 10, 99.90234375), (0.2, 5, 67.232)):
+        cls = [dict(C64, gamma=gamma, iters=I)]
+        patches, sel, _ = run_gpu(fse, cls, const, mask, blocks)
+        assert np.all(sel[0][:, :I] == 0)
+        np.testing.assert_allclose(patches, expect, atol=2e-3)
+    yy, xx = np.mgrid[0:H, 0:W]
+    alt = (50.0 * (-1.0) ** (yy + xx)).astype(np.float32)[None]
+    cls = [dict(C64, gamma=1.0, iters=1)]
+    patches, sel, _ = run_gpu(fse, cls, alt, mask, blocks)
+    assert np.all(sel[0][:, 0] == 32 * 64 + 32)
+    want = np.concatenate([alt[0, y:y + 16, x:x + 16].ravel() for _, x, y, _c in blocks])
+    np.testing.assert_allclose(patches, want, atol=1e-3)
+
+
+def test_determinism_trace_and_host_entry(fse):
+    """Bit-identical results: repeated runs, trace on/off, and the host-buffer
+    entry point."""
+    img = synth.make_image(13, 256, 256)[None]
+    blocks = synth.grid_losses(14, 256, 256, 16, 0.2, non_adjacent=True)
+    mask = synth.loss_mask(blocks, [16], 1, 256, 256)
+    a, _, _ = run_gpu(fse, [C64], img, mask, blocks, trace=True)
+    b, _, _ = run_gpu(fse, [C64], img, mask, blocks, trace=False)
+    c, _, _ = run_gpu(fse, [C64], img, mask, blocks, trace=False)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(b, c)
+    eng = fse.Engine([C64])
+    h = eng.run_host(img, mask, blocks)
+    eng.close()
+    np.testing.assert_array_equal(h[:len(a)], a)
+
+
+def test_empty_batch_and_invalid_arguments(fse):
+    eng = fse.Engine([C64])
+    img = torch.zeros((1, 64, 64), dtype=torch.uint8, device="cuda")
+    mask = torch.zeros((1, 64, 64), dtype=torch.uint8, device="cuda")
+    patches = torch.full((256,), -7.0, device="cuda")
+    eng.run(img, mask, np.zeros((0, 4), np.int32), patches=patches)
+    for bad in ([[0, 50, 0, 0]], [[1, 0, 0, 0]], [[0, 0, 0, 3]], [[0, -1, 0, 0]]):
+        with pytest.raises(fse.FseError) as ei:
+            eng.run(img, mask, np.array(bad, np.int32), patches=patches)
+        assert ei.value.status == 1
+    torch.cuda.synchronize()
+    assert torch.all(patches == -7.0)      # nothing was launched
+    eng.close()
+    with pytest.raises(fse.FseError):
+        fse.Engine([dict(C64, fft=128)])
+    with pytest.raises(fse.FseError):
+        fse.Engine([dict(C64, gamma=2.5)])
+
+
+# ------------------------------------------- full-size launch, sampled check
+def test_full_size_throughput_config_sampled(fse):
+    """The launch the benchmark times (64 x 3840x2160 u8 frames, 10% 16x16
+    losses, F=64, I=200): outputs are bit-identical with and without the
+    trace, and 48 sampled blocks match the oracle (guided replay)."""
+    T, H, W = 64, 2160, 3840
+    vid = synth.make_video_torch(21, T, H, W, device="cuda")
+    blocks = np.concatenate([synth.grid_losses(1000 + t, H, W, 16, 0.10, image=t) for t in range(T)])
+    mask_np = synth.loss_mask(blocks, [16], T, H, W)
+    dmask = torch.from_numpy(mask_np).cuda()
+    n = len(blocks)
+    res = {}
+    for trace in (False, True):
+        eng = fse.Engine([C64], trace=trace)
+        patches = torch.zeros(n * 256, dtype=torch.float32, device="cuda")
+        eng.run(vid, dmask, blocks, patches=patches)
+        torch.cuda.synchronize()
+        res[trace] = (patches.cpu().numpy(), eng.trace()[:2] if trace else None)
+        eng.close()
+    np.testing.assert_array_equal(res[False][0], res[True][0])
+    rng = np.random.default_rng(5)
+    pick = np.sort(rng.choice(n, 48, replace=False))
+    frames = sorted(set(int(blocks[i, 0]) for i in pick))
+    host = {f: vid[f].cpu().numpy() for f in frames}
+    sel, energy = res[True][1]
+    out = []
+    for i in pick:
+        bk = blocks[i].copy()
+        f = int(bk[0])
+        bk[0] = 0
+        p = res[True][0][256 * i:256 * (i + 1)].reshape(16, 16).astype(np.float64)
+        out.append(parity.check_block(host[f], mask_np[f], bk, [C64], p, sel[i], energy[i]))
+    s = parity.summarize(out)
+    print("full-size sample:", s)
+    assert s["ok"], s
