@@ -66,7 +66,7 @@ typedef enum {
  *   border d, width of the support frame around B, d >= 1, b + 2d <= fft
  *   fft    F, FFT size and DFT period: 16, 32 or 64 (Section IV uses 64x64)
  *   rho    rho-hat of Eq. (3), 0 < rho <= 1
- *   gamma  orthogonality-deficiency compensation factor of Eq. (9),
+ *   gamma  orthogonality-deficiency compensation factor of Eq. (13),
  *          0 < gamma < 2 (the paper uses values in (0, 1])
  *   iters  I, number of selected basis functions (Algorithm 1), 0 <= I <= 4096
  */

@@ -20,7 +20,7 @@
  *
  * Readings of points the paper leaves open (also listed in the design notes):
  *   - the DFT period is the FFT size F (Eq. (1) writes M, N; Section IV uses a
- *     64x64 FFT for a 48x48 area), so "MN" in Eq. (8) is F*F;
+ *     64x64 FFT for a 48x48 area), so "MN" in Eq. (15) is F*F;
  *   - argmax ties go to the smallest linear index k*F+l;
  *   - a support with zero total weight (W[0,0] == 0) yields the zero model.
  */

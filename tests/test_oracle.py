@@ -141,7 +141,7 @@ def test_real_input_brute_force_modulo_mirror():
 def test_energy_identity_and_monotone_decrease():
     """E_nu = sum w |s - g_nu|^2 drops by exactly gamma (2 - gamma)
     |R_w[u,v]|^2 / W[0,0] per iteration (from the projection of Section III
-    and the coefficient of Eq. (9)), so it never increases for 0 < gamma < 2."""
+    and the coefficient of Eq. (13)), so it never increases for 0 < gamma < 2."""
     F, I = 16, 40
     rng = np.random.default_rng(5)
     s = rng.normal(120, 40, (F, F))
@@ -164,7 +164,7 @@ def test_energy_identity_and_monotone_decrease():
 
 
 def test_incremental_residual_equals_recomputed():
-    """R_w after the updates of Eq. (11) equals FFT{w (s - g)} from scratch."""
+    """R_w after the updates of Eq. (18) equals FFT{w (s - g)} from scratch."""
     F, I = 64, 60
     rng = np.random.default_rng(9)
     s = rng.normal(120, 40, (F, F))
