@@ -161,8 +161,42 @@ fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dty
 fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef,
                          size_t cap, int *stride_out);
 
-/* Reason for the last failure on h (or of fse_create when h is NULL);
- * never NULL; valid until the next call on h. */
+/*
+ * Batch concealment that allocates nothing, for callers that may not call
+ * cudaMalloc (the paper has no counterpart: this is a deployment variant).
+ * Some programs cannot let a library allocate device memory once they run:
+ * cudaMalloc / cudaFree can synchronise the whole device, which a real-time
+ * video pipeline cannot afford; some applications give all device memory to
+ * their own pool allocator at start-up; some certified or embedded processes
+ * forbid allocation after initialisation.  This entry point needs no handle:
+ * the work-queue head, bucketed block list and weight / twiddle tables live
+ * in one fixed file-scope device array of about 3.1 MB that every GPU which
+ * loads the library holds until the process exits.
+ *   classes, n_classes   the size classes (as fse_config.cls), 1..4
+ *   images, dtype, n_images, height, width, pitch_bytes, loss_mask
+ *                        device buffers, as fse_extrapolate_batch
+ *   blocks               HOST array of n_blocks descriptors, n_blocks <= 65536
+ *                        (larger batches are rejected with
+ *                        FSE_ERR_INVALID_ARG; split them)
+ *   out                  device FP32 image; only B samples are written
+ *   cuda_stream          stream to enqueue on; the current device is used
+ * The first call on a device looks up the array's device address and the
+ * kernel's occupancy (once per device); make that first call before any
+ * stream capture.  All calls on a device share the array and it keeps the
+ * last call's contents: each call rewrites what it reads and zeroes the
+ * queue head, but calls whose GPU work overlaps (other streams or threads)
+ * race on it and must be serialised by the caller.  The host block list is
+ * copied from pageable memory, so the call waits for earlier work on the
+ * stream before it returns.  Errors: fse_last_error(NULL).
+ */
+fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, int n_classes, const void *images,
+                                         int dtype, int n_images, int height, int width,
+                                         size_t pitch_bytes, const uint8_t *loss_mask,
+                                         const fse_block *blocks, int n_blocks, float *out,
+                                         void *cuda_stream);
+
+/* Reason for the last failure on h (or, when h is NULL, of fse_create or
+ * fse_extrapolate_batch_noalloc); never NULL; valid until the next call. */
 const char *fse_last_error(const fse_handle *h);
 
 /* Free everything the handle owns (synchronises its streams).  NULL is a no-op. */

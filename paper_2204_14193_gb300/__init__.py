@@ -17,7 +17,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["fse_class", "fse_config", "fse_block", "FseError", "fse_create", "fse_extrapolate_batch",
-           "fse_extrapolate_batch_host", "fse_get_trace", "fse_last_error", "fse_destroy", "Engine",
+           "fse_extrapolate_batch_host", "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_last_error", "fse_destroy", "Engine",
            "library_path", "FSE_DTYPE_U8", "FSE_DTYPE_F32", "FSE_FLAG_TRACE", "FSE_INIT_ZERO",
            "FSE_INIT_LEARNED"]
 
@@ -72,13 +72,15 @@ def _load():
                                                   vp, vp, vp]
             lib.fse_extrapolate_batch_host.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp,
                                                        c_int, vp, vp]
+            lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
+                                                          c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
             lib.fse_last_error.argtypes = [vp]
             lib.fse_last_error.restype = ctypes.c_char_p
             lib.fse_destroy.argtypes = [vp]
             lib.fse_destroy.restype = None
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
-                      "fse_get_trace"):
+                      "fse_extrapolate_batch_noalloc", "fse_get_trace"):
                 getattr(lib, n).restype = c_int
             _lib = lib
     return _lib
@@ -124,6 +126,23 @@ def fse_extrapolate_batch_host(h, images: np.ndarray, dtype: int, n_images: int,
                                             blocks.ctypes.data if n_blocks else None, n_blocks,
                                             patches.ctypes.data, stream)
     _check(st, h)
+
+
+def fse_extrapolate_batch_noalloc(classes, images: int, dtype: int, n_images: int, height: int,
+                                  width: int, pitch_bytes: int, loss_mask: int, blocks: np.ndarray,
+                                  n_blocks: int, out: int, stream: int | None) -> None:
+    """Handle-free entry point that allocates no device memory (its scratch is
+    a fixed array inside the library); ``classes`` is a list of class dicts,
+    ``blocks`` a host int32 [n, 4] array, the other buffers device pointers."""
+    arr = (fse_class * len(classes))(*[
+        fse_class(int(c["block"]), int(c["border"]), int(c["fft"]), float(c["rho"]), float(c["gamma"]),
+                  int(c["iters"])) for c in classes])
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+    st = _load().fse_extrapolate_batch_noalloc(arr, len(classes), images, dtype, n_images, height, width,
+                                               pitch_bytes, loss_mask,
+                                               blocks.ctypes.data if n_blocks else None, n_blocks, out,
+                                               stream)
+    _check(st, None)
 
 
 def fse_get_trace(h, n_blocks: int):

@@ -62,6 +62,10 @@ uint64_t hash_words(const void *data, size_t n, uint64_t h) {
 
 }  // namespace
 
+// Sets the text fse_last_error(NULL) returns (used by the handle-free entry
+// point in fse_noalloc.cu).
+void fse_internal_set_global_error(const char *msg) { g_create_error = msg; }
+
 struct fse_handle {
     fse_config cfg{};
     int device = 0;
