@@ -121,6 +121,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_sm_clock_mhz(gpu: int) -> float:
+    """Maximum SM clock reported by nvidia-smi (fallback when the timed
+    region was too short to sample the clock)."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(gpu), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return float(out.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return 2070.0
+
+
 def profile_traffic():
     """DRAM bytes per launch recorded by the committed ncu summary, if it was
     taken on the current kernel source; else None."""
@@ -246,11 +257,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
             eng.run(vid, mask, blocks, patches=patches)
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
@@ -291,7 +304,7 @@ def main():
     F, I = cls["fft"], cls["iters"]
     smem_bytes_block = 8.0 * max(I - 1, 0) * F * F          # W reads of the residual updates
     flops_block = I * F * F * 11.0 + 3 * 5.0 * F * F * np.log2(F * F)
-    sm_mhz = clocks["sm_mhz"] or 1e-6 * props.clock_rate * 1e3
+    sm_mhz = clocks["sm_mhz"] or clocks["sm_max_mhz"] or max_sm_clock_mhz(local)
     achieved = n_blocks * smem_bytes_block / (ms / 1e3) / 1e9
     peak = sms * 128.0 * sm_mhz * 1e6 / 1e9
     fp32_peak = sms * 256.0 * sm_mhz * 1e6 / 1e12

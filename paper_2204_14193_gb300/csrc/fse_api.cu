@@ -16,7 +16,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/fse.h"
+#include "fse.h"
 #include "fse_device.cuh"
 
 using fse::BlockRec;
@@ -70,7 +70,8 @@ struct fse_handle {
     fse_config cfg{};
     int device = 0;
     int sm_count = 0;
-    int max_ctas_per_sm = 1;
+    int max_ctas_per_sm = 1;       // of the 128-thread kernel
+    int max_ctas_per_sm_256 = 1;   // of the 256-thread kernel
     size_t smem_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     float *d_wtab[FSE_MAX_CLASSES] = {};
@@ -96,8 +97,9 @@ struct fse_handle {
     cudaGraphExec_t gexec = nullptr;
     DevParams params{};
     int grid = 0;
-    // autotuner: chosen CTAs per SM, per class-mix signature
-    std::vector<std::pair<uint64_t, int>> tuned;
+    int nt = 128;                  // threads per CTA of the captured launch
+    // autotuner: chosen (threads per CTA, CTAs per SM) per class-mix signature
+    std::vector<std::pair<uint64_t, std::pair<int, int>>> tuned;
     // host-buffer staging
     void *d_img = nullptr;
     size_t img_cap = 0;
@@ -269,11 +271,14 @@ fse_status grow(fse_handle *h, T **ptr, size_t *cap, size_t need) {
     return FSE_OK;
 }
 
-fse_status capture_graph(fse_handle *h, int grid, cudaGraphExec_t *out) {
+fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     FSE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
-    fse::fse_batch_kernel<<<grid, fse::kThreads, h->smem_bytes, h->cap_stream>>>(h->params);
+    if (nt == 256)
+        fse::fse_batch_kernel<256><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params);
+    else
+        fse::fse_batch_kernel<128><<<grid, 128, h->smem_bytes, h->cap_stream>>>(h->params);
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -287,47 +292,53 @@ fse_status capture_graph(fse_handle *h, int grid, cudaGraphExec_t *out) {
     return FSE_OK;
 }
 
-// Autotuner: time each candidate grid (CTAs per SM) on the actual batch --
-// the outputs are identical for every candidate, so the runs are harmless --
-// and keep the fastest per class-mix signature.
-fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *best_cps) {
+// Autotuner: time each candidate mapping -- 128 threads per CTA (32 bins per
+// thread) or 256 (16 bins per thread), 1..3 CTAs per SM -- on the actual
+// batch (the outputs are identical for every candidate, so the runs are
+// harmless) and keep the fastest per class-mix signature.
+fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *best_nt, int *best_cps) {
     for (auto &kv : h->tuned)
         if (kv.first == pl.mix_sig) {
-            *best_cps = kv.second;
+            *best_nt = kv.second.first;
+            *best_cps = kv.second.second;
             return FSE_OK;
         }
-    const int maxc = h->max_ctas_per_sm;
-    int best = maxc;
+    int bnt = 256, bcps = h->max_ctas_per_sm_256;
     // small batches cannot fill the machine: no measurement needed
-    if ((long long)pl.total_items >= 2LL * h->sm_count && maxc > 1) {
+    if ((long long)pl.total_items >= 2LL * h->sm_count) {
         cudaEvent_t e0, e1;
         FSE_CUDA(h, cudaEventCreate(&e0));
         FSE_CUDA(h, cudaEventCreate(&e1));
         float best_ms = 1e30f;
-        for (int cps = 1; cps <= maxc; ++cps) {
-            const int grid = std::min(pl.total_items, cps * h->sm_count);
-            cudaGraphExec_t ex = nullptr;
-            fse_status st = capture_graph(h, grid, &ex);
-            if (st != FSE_OK) return st;
-            cudaGraphLaunch(ex, stream);  // warm-up
-            cudaEventRecord(e0, stream);
-            cudaGraphLaunch(ex, stream);
-            cudaEventRecord(e1, stream);
-            cudaError_t se = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            cudaGraphExecDestroy(ex);
-            if (se != cudaSuccess) return cuda_fail(h, se, "autotune run");
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = cps;
+        for (int nt : {128, 256}) {
+            const int maxc = nt == 256 ? h->max_ctas_per_sm_256 : h->max_ctas_per_sm;
+            for (int cps = std::max(1, maxc - 1); cps <= maxc; ++cps) {
+                const int grid = std::min(pl.total_items, cps * h->sm_count);
+                cudaGraphExec_t ex = nullptr;
+                fse_status st = capture_graph(h, nt, grid, &ex);
+                if (st != FSE_OK) return st;
+                cudaGraphLaunch(ex, stream);  // warm-up
+                cudaEventRecord(e0, stream);
+                cudaGraphLaunch(ex, stream);
+                cudaEventRecord(e1, stream);
+                cudaError_t se = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                cudaGraphExecDestroy(ex);
+                if (se != cudaSuccess) return cuda_fail(h, se, "autotune run");
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bnt = nt;
+                    bcps = cps;
+                }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    h->tuned.emplace_back(pl.mix_sig, best);
-    *best_cps = best;
+    h->tuned.emplace_back(pl.mix_sig, std::make_pair(bnt, bcps));
+    *best_nt = bnt;
+    *best_cps = bcps;
     return FSE_OK;
 }
 
@@ -438,11 +449,12 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     P.tr_coef = trace ? h->d_tr_coef : nullptr;
     P.tr_stride = stride;
     P.tw = h->d_tw;
-    int cps = h->max_ctas_per_sm;
-    st = autotune(h, pl, stream, &cps);
+    int nt = 256, cps = h->max_ctas_per_sm_256;
+    st = autotune(h, pl, stream, &nt, &cps);
     if (st != FSE_OK) return st;
+    h->nt = nt;
     h->grid = std::max(1, std::min(pl.total_items, cps * h->sm_count));
-    st = capture_graph(h, h->grid, &h->gexec);
+    st = capture_graph(h, nt, h->grid, &h->gexec);
     if (st != FSE_OK) return st;
     h->graph_valid = true;
     h->plan_key = key;
@@ -487,11 +499,16 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
         smem = std::max(smem, (size_t)(4096 / (F * F)) * 16 * F * F);
     }
     h->smem_bytes = smem;
-    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int occ = 0;
-    CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel, fse::kThreads, smem));
-    if (occ < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
+    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int occ = 0, occ2 = 0;
+    CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, smem));
+    CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fse::fse_batch_kernel<256>, 256, smem));
+    if (occ < 1 || occ2 < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
     h->max_ctas_per_sm = occ;
+    h->max_ctas_per_sm_256 = occ2;
     CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CREATE_CUDA(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming));
     CREATE_CUDA(cudaMalloc(&h->d_counter, sizeof(int)));

@@ -1,9 +1,9 @@
 // fse_device.cuh -- sm_103a device code of the cFSE hot path.
 //
 // One persistent kernel conceals every lost block of a batch.  A CTA has 128
-// threads and pulls work items from an atomic counter; an item is one F=64
-// block, four F=32 blocks or sixteen F=16 blocks, so every thread always owns
-// 32 frequency bins of one block.  Per block (Algorithm 1):
+// or 256 threads and pulls work items from an atomic counter; an item is one
+// F=64 block, four F=32 blocks or sixteen F=16 blocks, so every thread always
+// owns 32 (or 16) frequency bins of one block.  Per block (Algorithm 1):
 //   gather + Eq. (3) weights  -> z = w s + j alpha w on the F x F grid (smem)
 //   one complex FFT2 of z      -> R_w = FFT{w s}, W = FFT{w} (real-input split)
 //   I iterations               -> argmax |R_w|^2, c = gamma R_w[u,v] / W[0,0],
@@ -11,10 +11,9 @@
 //   Re{g} on B                 -> g = sum c phi_(u,v), accumulated per selection
 //
 // Layout of one block's spectrum (F x F bins, k = row, l = column):
-//   thread t of the block (t < F*F/32) owns column c = t % (F/2) and its
-//   partner column c + F/2, on the 16 rows k_i = t / (F/2) + i * (F/16).  The
-//   32 residual values live in registers as packed f32x2 pairs
-//   (R[k_i][c], R[k_i][c+F/2]).
+//   thread t of the block owns column c = t % (F/2) and its partner column
+//   c + F/2, on PAIRS rows k_i = t / (F/2) + i * (F/PAIRS).  The residual
+//   values live in registers as packed f32x2 pairs (R[k_i][c], R[k_i][c+F/2]).
 //   W lives in shared memory in a "dual chunk" layout: chunk (r, q), q < F,
 //   is 16 bytes {Re W[r][q], Re W[r][q+F/2], Im W[r][q], Im W[r][q+F/2]}
 //   (column indices mod F).  The shifted operand W[k_i-u][c-v],
@@ -28,8 +27,6 @@
 
 namespace fse {
 
-constexpr int kThreads = 128;   // threads per CTA, every class
-constexpr int kMaxPix = 8;      // B samples per thread (b*b <= 8 * F*F/32)
 constexpr int kMaxClasses = 4;
 
 struct DevClass {
@@ -133,40 +130,65 @@ __device__ __forceinline__ void dftR(float2 *x) {
 }
 
 // --------------------------------------------------------- group utilities
-// A "group" is the set of threads working on one block: the whole CTA for
-// F = 64 (4 warps), one warp for F = 32, eight lanes for F = 16.
-template <int F>
+// A "group" is the set of threads working on one block.  A CTA of NT threads
+// gives every thread PAIRS = 2048 / NT register pairs (2 * PAIRS bins), so a
+// block of F x F bins needs TB = F*F / (2 * PAIRS) threads and a work item
+// holds NT / TB = 4096 / F^2 blocks whatever NT is.
+//   NT = 128 (16 pairs): F=64 -> 4 warps, F=32 -> 1 warp, F=16 -> 8 lanes
+//   NT = 256 ( 8 pairs): F=64 -> 8 warps, F=32 -> 2 warps, F=16 -> 16 lanes
+template <int F, int PAIRS>
 struct Geo {
-    static constexpr int TB = F * F / 32;            // threads per block
+    static constexpr int TB = F * F / (2 * PAIRS);   // threads per block
     static constexpr int LPR = F / 2;                // lanes per spectrum row
-    static constexpr int RSTEP = F / 16;             // row step between a thread's rows
+    static constexpr int RSTEP = TB / LPR;           // row step between a thread's rows
     static constexpr int REGION = 16 * F * F;        // smem bytes per block
     static constexpr int FP = F + 1;                 // padded row of the FFT buffer
     static constexpr int R1 = (F == 16) ? 4 : 8;     // four-step FFT radices
     static constexpr int R2 = F / R1;
-    static constexpr int BPI = kThreads / TB;        // blocks per item
+    static constexpr int WPG = TB >= 32 ? TB / 32 : 1;   // warps per group
+    static constexpr int LANES = TB < 32 ? TB : 32;      // lanes per group and warp
+    static constexpr int NQ = PAIRS / 4;                 // quartets of pairs
+    static_assert(RSTEP * PAIRS == F, "thread rows must tile the spectrum");
 };
 
-template <int F>
-__device__ __forceinline__ void gsync(unsigned amask) {
-    if constexpr (F == 64) __syncthreads();
-    else __syncwarp(amask);
+constexpr int kMaxWarps = 8;
+
+struct RedShared {
+    uint4 win[2][kMaxWarps];   // per-warp argmax candidates, double-buffered by iteration parity
+    float sum[kMaxWarps];
+};
+
+struct Grp {
+    int g;            // group index inside the CTA
+    int lt;           // thread index inside the group
+    unsigned amask;   // lanes of this warp that belong to active groups
+};
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <int F>
-__device__ __forceinline__ float group_sum(float v, unsigned amask, float *s_buf) {
-    constexpr int TB = Geo<F>::TB;
-    constexpr int W = TB < 32 ? TB : 32;
+template <int F, int PAIRS, int NT>
+__device__ __forceinline__ void gsync(const Grp &gr) {
+    using G = Geo<F, PAIRS>;
+    if constexpr (G::TB == NT) __syncthreads();
+    else if constexpr (G::TB > 32) named_barrier(1 + gr.g, G::TB);
+    else __syncwarp(gr.amask);
+}
+
+template <int F, int PAIRS, int NT>
+__device__ __forceinline__ float group_sum(float v, const Grp &gr, RedShared *rs) {
+    using G = Geo<F, PAIRS>;
 #pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(amask, v, o);
-    if constexpr (TB > 32) {
+    for (int o = G::LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gr.amask, v, o);
+    if constexpr (G::TB > 32) {
         const int warp = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) s_buf[warp] = v;
-        __syncthreads();
+        if ((threadIdx.x & 31) == 0) rs->sum[warp] = v;
+        gsync<F, PAIRS, NT>(gr);
         float t = 0.f;
 #pragma unroll
-        for (int i = 0; i < TB / 32; ++i) t += s_buf[i];
-        __syncthreads();
+        for (int i = 0; i < G::WPG; ++i) t += rs->sum[gr.g * G::WPG + i];
+        gsync<F, PAIRS, NT>(gr);
         return t;
     }
     return v;
@@ -180,15 +202,18 @@ __device__ __forceinline__ float group_sum(float v, unsigned amask, float *s_buf
 //   step 2: for each (line, k1): DFT_R2 over n2 of the values at R2 k1 + n2,
 //           stored at k1 + R1 k2 (all loads before all stores).
 // ROWS selects rows (element stride 1) or columns (element stride FP).
-template <int F, bool ROWS>
-__device__ __forceinline__ void fft_pass(float2 *Z, const float2 *s_tw, int lt, unsigned amask) {
-    using G = Geo<F>;
+template <int F, int PAIRS, int NT, bool ROWS>
+__device__ __forceinline__ void fft_pass(float2 *Z, const float2 *s_tw, const Grp &gr) {
+    using G = Geo<F, PAIRS>;
     constexpr int TB = G::TB, R1 = G::R1, R2 = G::R2, FP = G::FP;
     constexpr int LS = ROWS ? FP : 1;     // line stride
     constexpr int ES = ROWS ? 1 : FP;     // element stride
-    // step 1
+    constexpr int N1 = F * R2 / TB;       // step-1 tasks per thread
+    constexpr int N2 = F * R1 / TB;       // step-2 tasks per thread
+    static_assert(N1 * TB == F * R2 && N2 * TB == F * R1, "FFT tasks must tile the group");
 #pragma unroll
-    for (int t = lt; t < F * R2; t += TB) {
+    for (int j = 0; j < N1; ++j) {
+        const int t = gr.lt + j * TB;
         const int line = t % F, n2 = t / F;
         float2 x[R1];
 #pragma unroll
@@ -200,27 +225,25 @@ __device__ __forceinline__ void fft_pass(float2 *Z, const float2 *s_tw, int lt, 
             Z[line * LS + (R2 * k1 + n2) * ES] = cmul_conj_tw(x[k1], tw);
         }
     }
-    gsync<F>(amask);
-    // step 2
-    constexpr int NT = F * R1 / TB;       // tasks per thread
-    float2 y[NT][R2];
+    gsync<F, PAIRS, NT>(gr);
+    float2 y[N2][R2];
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        const int t = lt + j * TB;
+    for (int j = 0; j < N2; ++j) {
+        const int t = gr.lt + j * TB;
         const int line = t % F, k1 = t / F;
 #pragma unroll
         for (int n2 = 0; n2 < R2; ++n2) y[j][n2] = Z[line * LS + (R2 * k1 + n2) * ES];
         dftR<R2>(y[j]);
     }
-    gsync<F>(amask);
+    gsync<F, PAIRS, NT>(gr);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        const int t = lt + j * TB;
+    for (int j = 0; j < N2; ++j) {
+        const int t = gr.lt + j * TB;
         const int line = t % F, k1 = t / F;
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) Z[line * LS + (k1 + R1 * k2) * ES] = y[j][k2];
     }
-    gsync<F>(amask);
+    gsync<F, PAIRS, NT>(gr);
 }
 
 // ------------------------------------------------------- argmax reduction
@@ -246,86 +269,97 @@ __device__ __forceinline__ bool search_quartet(const uint64_t *Rre, const uint64
 }
 
 // Search all bins of this thread for energy M (the thread's max equals M).
-// Returns the local slot (2 i + h) or -1, with the residual at that bin.
+// Quartets are checked in order, so the first hit has the smallest linear
+// index.  Returns the local slot (2 i + h) or -1, with the residual there.
+template <int NQ>
 __device__ __forceinline__ int thread_search(const uint64_t *Rre, const uint64_t *Rim, const float *q,
                                              uint32_t M, float &rr, float &ri) {
     int hit = -1;
     bool done = false;
     if (__float_as_uint(q[0]) == M) done = search_quartet<0>(Rre, Rim, M, hit, rr, ri);
     if (!done && __float_as_uint(q[1]) == M) done = search_quartet<1>(Rre, Rim, M, hit, rr, ri);
-    if (!done && __float_as_uint(q[2]) == M) done = search_quartet<2>(Rre, Rim, M, hit, rr, ri);
-    if (!done && __float_as_uint(q[3]) == M) done = search_quartet<3>(Rre, Rim, M, hit, rr, ri);
+    if constexpr (NQ > 2) {
+        if (!done && __float_as_uint(q[2]) == M) done = search_quartet<2>(Rre, Rim, M, hit, rr, ri);
+        if (!done && __float_as_uint(q[3]) == M) done = search_quartet<3>(Rre, Rim, M, hit, rr, ri);
+    }
     return hit;
 }
 
-struct RedShared {
-    uint32_t red[4];
-    uint4 win[4];
-    float sum[4];
-};
-
 // Group-wide argmax of |R_w|^2 with ties to the smallest linear index.
-// tmax: this thread's max energy; q: its quartet maxima.
-template <int F>
+// tmax: this thread's max energy; q: its quartet maxima; parity: iteration
+// parity (double-buffers the cross-warp exchange).
+//
+// Every warp-wide step (shuffle, redux, shared-memory exchange) waits in the
+// SM's memory-instruction queue behind the residual update's 16-byte loads,
+// so the reduction is built from as few DEPENDENT such steps as possible:
+// one redux.sync for the max, the owner's register search, one redux.sync for
+// the smallest index, and (multi-warp groups) one shared-memory exchange.
+template <int F, int PAIRS, int NT>
 __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t *Rim, float tmax,
-                                             const float *q, int lt, unsigned amask, RedShared *rs) {
-    using G = Geo<F>;
+                                             const float *q, const Grp &gr, RedShared *rs, int parity) {
+    using G = Geo<F, PAIRS>;
     const uint32_t mt = __float_as_uint(tmax);
-    const int c0 = lt % G::LPR, r0 = lt / G::LPR;
+    const int c0 = gr.lt % G::LPR, r0 = gr.lt / G::LPR;
     auto lin = [&](int slot) -> uint32_t {      // slot -> linear bin index
         const int i = slot >> 1, h = slot & 1;
         return (uint32_t)((r0 + i * G::RSTEP) * F + c0 + h * (F / 2));
     };
+    const int lane = threadIdx.x & 31;
     Pick p;
-    if constexpr (F == 64) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (G::TB > 32) {
+        // whole warps: each warp finds its own candidate (max energy, smallest
+        // index, residual there), one exchange, every thread picks the best
+        const int warp = threadIdx.x >> 5;
+        const int w0 = gr.g * G::WPG;
         const uint32_t mw = __reduce_max_sync(0xffffffffu, mt);
-        if (lane == 0) rs->red[warp] = mw;
-        __syncthreads();
-        const uint4 r4 = *reinterpret_cast<const uint4 *>(rs->red);
-        const uint32_t M = max(max(r4.x, r4.y), max(r4.z, r4.w));
-        if (mw == M) {
-            uint32_t cand = 0xffffffffu;
-            float rr = 0.f, ri = 0.f;
-            if (mt == M) {
-                const int hit = thread_search(Rre, Rim, q, M, rr, ri);
-                if (hit >= 0) cand = lin(hit);
-            }
-            const uint32_t iw = __reduce_min_sync(0xffffffffu, cand);
-            if (cand == iw && cand != 0xffffffffu)
-                rs->win[warp] = make_uint4(iw, __float_as_uint(rr), __float_as_uint(ri), 0u);
+        uint32_t cand = 0xffffffffu;
+        float rr = 0.f, ri = 0.f;
+        if (mt == mw) {
+            const int hit = thread_search<G::NQ>(Rre, Rim, q, mw, rr, ri);
+            if (hit >= 0) cand = lin(hit);
         }
-        __syncthreads();
-        p.idx = 0xffffffffu; p.rr = 0.f; p.ri = 0.f; p.ebits = M;
-        const uint32_t rw[4] = {r4.x, r4.y, r4.z, r4.w};
+        const uint32_t iw = __reduce_min_sync(0xffffffffu, cand);
+        uint4 *win = rs->win[parity];
+        if ((cand == iw && cand != 0xffffffffu) || (iw == 0xffffffffu && lane == 0))
+            win[warp] = make_uint4(mw, iw, __float_as_uint(rr), __float_as_uint(ri));
+        gsync<F, PAIRS, NT>(gr);
+        p.idx = 0xffffffffu; p.rr = 0.f; p.ri = 0.f; p.ebits = 0u;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            if (rw[w] == M) {
-                const uint4 e = rs->win[w];
-                if (e.x < p.idx) { p.idx = e.x; p.rr = __uint_as_float(e.y); p.ri = __uint_as_float(e.z); }
+        for (int i = 0; i < G::WPG; ++i) {
+            const uint4 e = win[w0 + i];
+            if (e.x > p.ebits || (e.x == p.ebits && e.y < p.idx)) {
+                p.ebits = e.x; p.idx = e.y; p.rr = __uint_as_float(e.z); p.ri = __uint_as_float(e.w);
             }
         }
     } else {
-        constexpr int W = G::TB;                  // 32 (F=32) or 8 (F=16) lanes
-        uint32_t M = mt;
+        constexpr int W = G::LANES;               // lanes of one group (8, 16 or 32)
+        constexpr int NG = 32 / W;                // groups per warp
+        const int mygrp = lane / W;
+        // one redux per group; they do not depend on each other
+        uint32_t M = 0u;
 #pragma unroll
-        for (int o = W / 2; o > 0; o >>= 1) M = max(M, __shfl_xor_sync(amask, M, o));
+        for (int k = 0; k < NG; ++k) {
+            const uint32_t r = __reduce_max_sync(gr.amask, mygrp == k ? mt : 0u);
+            if (mygrp == k) M = r;
+        }
         uint32_t cand = 0xffffffffu;
         float rr = 0.f, ri = 0.f;
         if (mt == M) {
-            const int hit = thread_search(Rre, Rim, q, M, rr, ri);
+            const int hit = thread_search<G::NQ>(Rre, Rim, q, M, rr, ri);
             if (hit >= 0) cand = lin(hit);
         }
-        uint32_t iw = cand;
+        uint32_t iw = 0xffffffffu;
 #pragma unroll
-        for (int o = W / 2; o > 0; o >>= 1) iw = min(iw, __shfl_xor_sync(amask, iw, o));
-        const int lane = threadIdx.x & 31;
-        const unsigned gm = (W == 32) ? 0xffffffffu : (0xffu << (lane & ~7));
-        const unsigned who = __ballot_sync(amask, cand == iw) & gm;
+        for (int k = 0; k < NG; ++k) {
+            const uint32_t r = __reduce_min_sync(gr.amask, mygrp == k ? cand : 0xffffffffu);
+            if (mygrp == k) iw = r;
+        }
+        const unsigned gm = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << (lane & ~(W - 1)));
+        const unsigned who = __ballot_sync(gr.amask, cand == iw) & gm;
         const int src = who ? __ffs(who) - 1 : (lane & ~(W - 1));
-        p.idx = (iw == 0xffffffffu) ? 0xffffffffu : iw;
-        p.rr = __shfl_sync(amask, rr, src);
-        p.ri = __shfl_sync(amask, ri, src);
+        p.idx = iw;
+        p.rr = __shfl_sync(gr.amask, rr, src);
+        p.ri = __shfl_sync(gr.amask, ri, src);
         p.ebits = M;
     }
     if (p.idx == 0xffffffffu) { p.idx = 0; p.rr = 0.f; p.ri = 0.f; }
@@ -333,51 +367,63 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 }
 
 // ------------------------------------------------------- per-block worker
-template <int F>
+// NP: B samples per thread (compile time; the caller picks the smallest
+// variant that covers b*b).
+template <int F, int PAIRS, int NT, int NP>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
-    using G = Geo<F>;
-    constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP;
-    const int gidx = threadIdx.x / TB;
-    const int lt = threadIdx.x % TB;
-    const bool active = gidx < count;
-    const unsigned amask = __ballot_sync(0xffffffffu, active);
+    using G = Geo<F, PAIRS>;
+    constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
+    Grp gr;
+    gr.g = threadIdx.x / TB;
+    gr.lt = threadIdx.x % TB;
+    const bool active = gr.g < count;
+    gr.amask = __ballot_sync(0xffffffffu, active);
     if (!active) return;
+    const int lt = gr.lt;
 
-    const BlockRec blk = P.blocks[first + gidx];
-    unsigned char *region = smem + gidx * G::REGION;
+    const BlockRec blk = P.blocks[first + gr.g];
+    unsigned char *region = smem + gr.g * G::REGION;
     float2 *Z = reinterpret_cast<float2 *>(region);
 
     const int b = C.b, d = C.d, M = C.M, off = C.off;
     // ---- S0/S1: gather the area, Eq. (3) weights, z = (w s, w) ----
+    // All loads of the thread's grid positions are issued first (clamped to
+    // the image, so always in bounds), then the weights are applied: one
+    // memory round trip instead of one per position.
+    constexpr int NPOS = F * F / TB;
+    float sv[NPOS];
+    uint8_t mk[NPOS];
+#pragma unroll
+    for (int t = 0; t < NPOS; ++t) {
+        const int pix = lt + t * TB;
+        const int yy = min(max(blk.y - d + pix / F - off, 0), P.H - 1);
+        const int xx = min(max(blk.x - d + pix % F - off, 0), P.W - 1);
+        mk[t] = P.mask[((size_t)blk.image * P.H + yy) * P.W + xx];
+        const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+        sv[t] = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
+                             : reinterpret_cast<const float *>(row)[xx];
+    }
     float sws2 = 0.f, sw = 0.f;
-    for (int pix = lt; pix < F * F; pix += TB) {
+#pragma unroll
+    for (int t = 0; t < NPOS; ++t) {
+        const int pix = lt + t * TB;
         const int m = pix / F, n = pix % F;
         const int am = m - off, an = n - off;
-        float ws = 0.f, w = 0.f;
-        if (am >= 0 && am < M && an >= 0 && an < M) {
-            const int yy = blk.y - d + am, xx = blk.x - d + an;
-            const bool inB = am >= d && am < d + b && an >= d && an < d + b;
-            if (!inB && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W) {
-                const size_t mi = ((size_t)blk.image * P.H + yy) * P.W + xx;
-                if (P.mask[mi] == 0) {
-                    const char *row = static_cast<const char *>(P.images) +
-                                      ((long long)blk.image * P.H + yy) * P.pitch;
-                    const float s = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
-                                                 : reinterpret_cast<const float *>(row)[xx];
-                    w = __ldg(&C.wtab[am * M + an]);
-                    ws = w * s;
-                    sws2 = fmaf(ws, s, sws2);
-                    sw += w;
-                }
-            }
-        }
+        const int yy = blk.y - d + am, xx = blk.x - d + an;
+        const bool inA = am >= 0 && am < M && an >= 0 && an < M &&
+                         !(am >= d && am < d + b && an >= d && an < d + b) &&
+                         yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0;
+        const float w = inA ? __ldg(&C.wtab[am * M + an]) : 0.f;
+        const float ws = w * sv[t];
+        sws2 = fmaf(ws, sv[t], sws2);
+        sw += w;
         Z[m * FP + n] = make_float2(ws, w);
     }
     // alpha = power of two near the weighted RMS of s: balances the two real
     // signals packed into one complex FFT (exact scaling)
-    const float tsw = group_sum<F>(sw, amask, rsh->sum);
-    const float tsws2 = group_sum<F>(sws2, amask, rsh->sum);
+    const float tsw = group_sum<F, PAIRS, NT>(sw, gr, rsh);
+    const float tsws2 = group_sum<F, PAIRS, NT>(sws2, gr, rsh);
     float alpha = 1.f;
     if (tsw > 0.f && tsws2 > 0.f) {
         int e;
@@ -388,10 +434,10 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         const int m = pix / F, n = pix % F;
         Z[m * FP + n].y *= alpha;
     }
-    gsync<F>(amask);
+    gsync<F, PAIRS, NT>(gr);
     // ---- S2/S3: FFT2 of z ----
-    fft_pass<F, true>(Z, s_tw, lt, amask);
-    fft_pass<F, false>(Z, s_tw, lt, amask);
+    fft_pass<F, PAIRS, NT, true>(Z, s_tw, gr);
+    fft_pass<F, PAIRS, NT, false>(Z, s_tw, gr);
 
     // ---- split into R_w = FFT{w s} and W = FFT{w} ----
     // W chunk rows k >= F/2 + 1 lie beyond the padded FFT buffer, so they are
@@ -400,10 +446,10 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     const float ainv = 1.f / alpha;
     float4 *Wd = reinterpret_cast<float4 *>(region);
     constexpr int SAFE = F / 2 + 1;
-    uint64_t Rre[16], Rim[16];
-    float4 Wc[16];
+    uint64_t Rre[PAIRS], Rim[PAIRS];
+    float4 Wc[PAIRS];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < PAIRS; ++i) {
         const int k = r0 + i * RSTEP, km = (F - k) & (F - 1);
         float2 R2[2], W2[2];
 #pragma unroll
@@ -422,23 +468,23 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         }
     }
     const float W00 = Z[0].y * ainv;
-    gsync<F>(amask);
+    gsync<F, PAIRS, NT>(gr);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < PAIRS; ++i) {
         const int k = r0 + i * RSTEP;
         if (i * RSTEP < SAFE && k < SAFE) {
             Wd[k * F + c0] = Wc[i];
             Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
-    gsync<F>(amask);
+    gsync<F, PAIRS, NT>(gr);
 
-    // ---- B samples owned by this thread ----
-    const int npix = (b * b + TB - 1) / TB;
-    int pm_[kMaxPix], pn_[kMaxPix];
-    float acc[kMaxPix];
+    // ---- B samples owned by this thread (NP of them; samples j >= b*b are
+    //      computed but never stored) ----
+    int pm_[NP], pn_[NP];
+    float acc[NP];
 #pragma unroll
-    for (int t = 0; t < kMaxPix; ++t) {
+    for (int t = 0; t < NP; ++t) {
         const int j = lt + t * TB;
         pm_[t] = off + d + j / b;
         pn_[t] = off + d + j % b;
@@ -448,23 +494,22 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     const float cg = C.gamma * W0bar;
 
     // ---- S5: first selection (energies of R_w^(0)) ----
-    float q[4];
-    float tmax;
-    {
+    float q[NQ];
+    float tmax = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t e0 = energy2(Rre[4 * j], Rim[4 * j]), e1 = energy2(Rre[4 * j + 1], Rim[4 * j + 1]);
-            const uint64_t e2 = energy2(Rre[4 * j + 2], Rim[4 * j + 2]), e3 = energy2(Rre[4 * j + 3], Rim[4 * j + 3]);
-            const float a = max3f(lo_of(e0), hi_of(e0), lo_of(e1));
-            const float bq = max3f(hi_of(e1), lo_of(e2), hi_of(e2));
-            q[j] = max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3)));
-        }
-        tmax = fmaxf(max3f(q[0], q[1], q[2]), q[3]);
+    for (int j = 0; j < NQ; ++j) {
+        const uint64_t e0 = energy2(Rre[4 * j], Rim[4 * j]), e1 = energy2(Rre[4 * j + 1], Rim[4 * j + 1]);
+        const uint64_t e2 = energy2(Rre[4 * j + 2], Rim[4 * j + 2]), e3 = energy2(Rre[4 * j + 3], Rim[4 * j + 3]);
+        const float a = max3f(lo_of(e0), hi_of(e0), lo_of(e1));
+        const float bq = max3f(hi_of(e1), lo_of(e2), hi_of(e2));
+        q[j] = max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3)));
+        tmax = fmaxf(tmax, q[j]);
     }
     const int iters = C.iters;
     Pick pick;
-    if (iters > 0) pick = group_argmax<F>(Rre, Rim, tmax, q, lt, amask, rsh);
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, 0);
 
+    const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
     for (int nu = 1; nu <= iters; ++nu) {
         // ---- S6/S7: coefficient and model ----
         const float cr = pick.rr * cg, ci = pick.ri * cg;
@@ -475,28 +520,40 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             P.tr_energy[o] = __uint_as_float(pick.ebits);
             P.tr_coef[o] = make_float2(cr, ci);
         }
+        // model update of this selection, evaluated on B: g += c phi_(u,v)
+        // (independent of the residual update and of the next reduction)
+        auto model = [&]() {
 #pragma unroll
-        for (int t = 0; t < kMaxPix; ++t) {
-            if (t < npix) {
+            for (int t = 0; t < NP; ++t) {
                 const int ph = (u * pm_[t] + v * pn_[t]) & (F - 1);
                 const float2 tw = s_tw[ph * (64 / F)];
                 acc[t] = fmaf(cr, tw.x, fmaf(-ci, tw.y, acc[t]));
             }
+        };
+        if (nu == iters) {
+            model();
+            break;
         }
-        if (nu == iters) break;
         // ---- S8: R_w[k,l] -= c W[k-u, l-v] fused with |R_w|^2 and max ----
         const uint64_t ncr = pk(-cr, -cr), pci = pk(ci, ci), nci = pk(-ci, -ci);
+        // Row of pair i is (r0 - u + i*RSTEP) mod F: it wraps once, at pair iw.
+        // Pairs before the wrap address from A, the others from A - F*F, so each
+        // load needs one select and an immediate offset.
         const int qcol = (c0 - v) & (F - 1);
-        const int rbase = r0 - u;
+        const int rb = (r0 - u) & (F - 1);
+        const int iw = (F - rb + RSTEP - 1) / RSTEP;
+        const ulonglong2 *A = Wq + rb * F + qcol;
+        const ulonglong2 *A2 = A - F * F;
+        tmax = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < NQ; ++j) {
             float ev[8];
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii) {
                 const int i = 4 * j + ii;
-                const int r = (rbase + i * RSTEP) & (F - 1);
-                const float4 w = Wd[r * F + qcol];
-                const uint64_t wre = pk(w.x, w.y), wim = pk(w.z, w.w);
+                // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
+                const ulonglong2 w = (i < iw ? A : A2)[i * RSTEP * F];
+                const uint64_t wre = w.x, wim = w.y;
                 uint64_t a = fma2(ncr, wre, Rre[i]);
                 Rre[i] = fma2(pci, wim, a);
                 uint64_t bb = fma2(ncr, wim, Rim[i]);
@@ -508,17 +565,18 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             const float a = max3f(ev[0], ev[1], ev[2]);
             const float bq = max3f(ev[3], ev[4], ev[5]);
             q[j] = max3f(a, bq, fmaxf(ev[6], ev[7]));
+            tmax = fmaxf(tmax, q[j]);
         }
-        tmax = fmaxf(max3f(q[0], q[1], q[2]), q[3]);
+        model();
         // ---- S5: next selection ----
-        pick = group_argmax<F>(Rre, Rim, tmax, q, lt, amask, rsh);
+        pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, nu & 1);
     }
 
     // ---- S10: write Re{g} on B ----
 #pragma unroll
-    for (int t = 0; t < kMaxPix; ++t) {
+    for (int t = 0; t < NP; ++t) {
         const int j = lt + t * TB;
-        if (t < npix && j < b * b) {
+        if (j < b * b) {
             const int pm = j / b, pn = j % b;
             if (P.out != nullptr)
                 P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = acc[t];
@@ -527,13 +585,27 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     }
 }
 
+template <int F, int PAIRS, int NT>
+__device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
+                                              unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
+    constexpr int TB = Geo<F, PAIRS>::TB;
+    constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
+    constexpr int NPL = PAIRS / 2;                // covers b <= F/2
+    if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS>(P, C, first, count, smem, s_tw, rsh);
+    else process<F, PAIRS, NT, NPL>(P, C, first, count, smem, s_tw, rsh);
+}
+
 // ------------------------------------------------------ persistent kernel
-__global__ void __launch_bounds__(kThreads, 3) fse_batch_kernel(const __grid_constant__ DevParams P) {
+// NT threads per CTA (128 or 256), 64 KB of dynamic shared memory, at most
+// three CTAs per SM.
+template <int NT>
+__global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant__ DevParams P) {
+    constexpr int PAIRS = 2048 / NT;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ float2 s_tw[64];
     __shared__ int s_item;
     __shared__ RedShared rsh;
-    for (int i = threadIdx.x; i < 64; i += kThreads) s_tw[i] = P.tw[i];
+    for (int i = threadIdx.x; i < 64; i += NT) s_tw[i] = P.tw[i];
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.counter, 1);
@@ -547,9 +619,9 @@ __global__ void __launch_bounds__(kThreads, 3) fse_batch_kernel(const __grid_con
         const int first = P.seg_block_start[sg] + (item - item0) * C.bpi;
         const int count = min(C.bpi, P.seg_block_start[sg] + P.seg_block_count[sg] - first);
         switch (C.F) {
-            case 64: process<64>(P, C, first, count, smem, s_tw, &rsh); break;
-            case 32: process<32>(P, C, first, count, smem, s_tw, &rsh); break;
-            default: process<16>(P, C, first, count, smem, s_tw, &rsh); break;
+            case 64: process_class<64, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+            case 32: process_class<32, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+            default: process_class<16, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
         }
         __syncthreads();
     }

@@ -25,7 +25,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/fse.h"
+#include "fse.h"
 
 namespace {
 #include "fse_device.cuh"   // private copy of the kernels (internal linkage)
@@ -151,11 +151,11 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess || !p) return fail(FSE_ERR_CUDA, "noalloc: cudaGetSymbolAddress(g_scratch) failed");
-            if (cudaFuncSetAttribute(fse::fse_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536) !=
+            if (cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536) !=
                 cudaSuccess)
                 return fail(FSE_ERR_CUDA, "noalloc: cannot set the kernel's shared-memory size");
             int occ = 0, sms = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel, fse::kThreads, 65536) !=
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, 65536) !=
                     cudaSuccess ||
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ < 1)
                 return fail(FSE_ERR_CUDA, "noalloc: occupancy query failed");
@@ -241,7 +241,7 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
     noalloc_bucket_kernel<<<1, 32 * FSE_MAX_CLASSES, 0, stream>>>(d_raw, n_blocks, d_rec, d_starts, n_classes);
     noalloc_setup_kernel<<<1, 1, 0, stream>>>(d_counter);
     const int grid = std::max(1, std::min(items, ds.ctas_per_sm * ds.sm_count));
-    fse::fse_batch_kernel<<<grid, fse::kThreads, 65536, stream>>>(P);
+    fse::fse_batch_kernel<128><<<grid, 128, 65536, stream>>>(P);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return fail(FSE_ERR_CUDA, "noalloc: kernel launch failed");
     return FSE_OK;
