@@ -57,7 +57,7 @@ def _load():
                                                 ctypes.c_int, ip, dp, dp, dp]
             for name in ("oracle_fft2", "oracle_cfse", "oracle_cfse_spatial"):
                 getattr(lib, name).restype = ctypes.c_int
-            if hasattr(lib, "oracle_conv2d_fwd"):
+            if hasattr(lib, "oracle_conv3x3_fwd"):
                 from . import cnn as _cnn  # noqa: F401  (registers CNN prototypes)
                 _cnn._register(lib)
             _lib = lib
