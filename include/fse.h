@@ -161,6 +161,57 @@ fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dty
 fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef,
                          size_t cap, int *stride_out);
 
+/* ------------------------------------------------------------------------
+ * Learned initialisation network (no counterpart in the paper).
+ *
+ * A small CNN estimates the whole extrapolation area from its support so
+ * that Algorithm 1 can start from the residual (fse_config.init =
+ * FSE_INIT_LEARNED).  Four 3x3 convolutions with "same" zero padding and
+ * dilations 1, 2, 4, 8, channels 2 -> 32 -> 32 -> 32 -> 1, ReLU after the
+ * first three; bfloat16 weights and activations, FP32 accumulation (tensor
+ * cores); FP32 gradients; Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master
+ * weights.  Input of one area (H x W, row-major, FP32): channel 0 = support
+ * sample / 255 on the support area and 0 elsewhere, channel 1 = 1 on the
+ * support area and 0 elsewhere.  Output: the estimate / 255.
+ * Parameters: one flat FP32 vector, per layer W[co][ci][ky][kx] then b[co].
+ * ------------------------------------------------------------------------ */
+#define FSE_CNN_PARAMS 19393
+typedef struct fse_cnn fse_cnn;
+
+/* Number of parameters (FSE_CNN_PARAMS). */
+size_t fse_cnn_param_count(void);
+
+/* Network state for areas of height x width on `device`, with buffers for up
+ * to max_batch areas per call; parameters start at zero. */
+fse_status fse_cnn_create(fse_cnn **out, int device, int height, int width, int max_batch);
+
+/* Copy n = FSE_CNN_PARAMS host FP32 parameters in (resets the Adam moments
+ * and step count) or out.  Synchronous. */
+fse_status fse_cnn_set_params(fse_cnn *c, const float *params, size_t n);
+fse_status fse_cnn_get_params(fse_cnn *c, float *params, size_t n);
+
+/* Inference on n areas: x device [n][2][H][W] FP32, y device [n][H][W] FP32.
+ * Asynchronous on cuda_stream. */
+fse_status fse_cnn_forward(fse_cnn *c, const float *x, int n, float *y, void *cuda_stream);
+
+/* Mean weighted squared error L = sum lam (y - target)^2 / (n H W) and its
+ * gradient with respect to every parameter.  target, lam: device [n][H][W]
+ * (lam NULL = all ones).  grad_host (FSE_CNN_PARAMS floats) and loss_host may
+ * be NULL.  Synchronises the stream. */
+fse_status fse_cnn_loss_grad(fse_cnn *c, const float *x, const float *target, const float *lam, int n,
+                             float *grad_host, float *loss_host, void *cuda_stream);
+
+/* One Adam step with learning rate lr on the loss above.  loss_host (the loss
+ * before the step) may be NULL, which keeps the call asynchronous. */
+fse_status fse_cnn_train_step(fse_cnn *c, const float *x, const float *target, const float *lam, int n,
+                              float lr, float *loss_host, void *cuda_stream);
+
+/* Reason for the last failure on c (or of fse_cnn_create when c is NULL). */
+const char *fse_cnn_last_error(const fse_cnn *c);
+
+/* Free the network state.  NULL is a no-op. */
+void fse_cnn_destroy(fse_cnn *c);
+
 /*
  * Batch concealment that allocates nothing, for callers that may not call
  * cudaMalloc (the paper has no counterpart: this is a deployment variant).

@@ -82,6 +82,21 @@ def _load():
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
                       "fse_extrapolate_batch_noalloc", "fse_get_trace"):
                 getattr(lib, n).restype = c_int
+            fp = ctypes.POINTER(ctypes.c_float)
+            lib.fse_cnn_param_count.restype = sz
+            lib.fse_cnn_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, c_int]
+            lib.fse_cnn_set_params.argtypes = [vp, vp, sz]
+            lib.fse_cnn_get_params.argtypes = [vp, vp, sz]
+            lib.fse_cnn_forward.argtypes = [vp, vp, c_int, vp, vp]
+            lib.fse_cnn_loss_grad.argtypes = [vp, vp, vp, vp, c_int, vp, fp, vp]
+            lib.fse_cnn_train_step.argtypes = [vp, vp, vp, vp, c_int, ctypes.c_float, fp, vp]
+            lib.fse_cnn_last_error.argtypes = [vp]
+            lib.fse_cnn_last_error.restype = ctypes.c_char_p
+            lib.fse_cnn_destroy.argtypes = [vp]
+            lib.fse_cnn_destroy.restype = None
+            for n in ("fse_cnn_create", "fse_cnn_set_params", "fse_cnn_get_params", "fse_cnn_forward",
+                      "fse_cnn_loss_grad", "fse_cnn_train_step"):
+                getattr(lib, n).restype = c_int
             _lib = lib
     return _lib
 
@@ -164,6 +179,112 @@ def fse_get_trace(h, n_blocks: int):
 def fse_destroy(h) -> None:
     if h is not None:
         _load().fse_destroy(h)
+
+
+# ------------------------------------------------ learned-init network ABI
+FSE_CNN_PARAMS = 19393
+
+
+def _cnn_check(status: int, c):
+    if status != 0:
+        raise FseError(status, _load().fse_cnn_last_error(c).decode())
+
+
+def fse_cnn_create(device: int, height: int, width: int, max_batch: int):
+    c = ctypes.c_void_p()
+    _cnn_check(_load().fse_cnn_create(ctypes.byref(c), device, height, width, max_batch), None)
+    return c
+
+
+def fse_cnn_set_params(c, params: np.ndarray) -> None:
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    _cnn_check(_load().fse_cnn_set_params(c, params.ctypes.data, params.size), c)
+
+
+def fse_cnn_get_params(c) -> np.ndarray:
+    out = np.zeros(FSE_CNN_PARAMS, np.float32)
+    _cnn_check(_load().fse_cnn_get_params(c, out.ctypes.data, out.size), c)
+    return out
+
+
+def fse_cnn_forward(c, x: int, n: int, y: int, stream: int | None) -> None:
+    _cnn_check(_load().fse_cnn_forward(c, x, n, y, stream), c)
+
+
+def fse_cnn_loss_grad(c, x: int, target: int, lam: int | None, n: int, stream: int | None):
+    g = np.zeros(FSE_CNN_PARAMS, np.float32)
+    loss = ctypes.c_float(0.0)
+    _cnn_check(_load().fse_cnn_loss_grad(c, x, target, lam, n, g.ctypes.data, ctypes.byref(loss), stream), c)
+    return float(loss.value), g
+
+
+def fse_cnn_train_step(c, x: int, target: int, lam: int | None, n: int, lr: float, stream: int | None,
+                       want_loss: bool = True):
+    loss = ctypes.c_float(0.0)
+    _cnn_check(_load().fse_cnn_train_step(c, x, target, lam, n, lr, ctypes.byref(loss) if want_loss else None,
+                                          stream), c)
+    return float(loss.value) if want_loss else None
+
+
+def fse_cnn_destroy(c) -> None:
+    if c is not None:
+        _load().fse_cnn_destroy(c)
+
+
+class Cnn:
+    """The learned-initialisation network on one device (torch tensors in,
+    torch tensors out; every computation runs in libfse.so)."""
+
+    def __init__(self, height: int = 48, width: int = 48, max_batch: int = 256, device: int = 0):
+        self.H, self.W, self.max_batch, self.device = height, width, max_batch, device
+        self.c = fse_cnn_create(device, height, width, max_batch)
+
+    def set_params(self, p):
+        fse_cnn_set_params(self.c, p)
+
+    def get_params(self):
+        return fse_cnn_get_params(self.c)
+
+    def _stream(self):
+        import torch
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def forward(self, x):
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.shape[1:] == (2, self.H, self.W)
+        y = torch.empty((x.shape[0], self.H, self.W), dtype=torch.float32, device=x.device)
+        fse_cnn_forward(self.c, x.data_ptr(), x.shape[0], y.data_ptr(), self._stream())
+        return y
+
+    def loss_grad(self, x, target, lam=None):
+        return fse_cnn_loss_grad(self.c, x.data_ptr(), target.data_ptr(),
+                                 lam.data_ptr() if lam is not None else None, x.shape[0], self._stream())
+
+    def train_step(self, x, target, lam=None, lr=1e-3, want_loss=True):
+        return fse_cnn_train_step(self.c, x.data_ptr(), target.data_ptr(),
+                                  lam.data_ptr() if lam is not None else None, x.shape[0], lr, self._stream(),
+                                  want_loss)
+
+    def close(self):
+        if self.c is not None:
+            fse_cnn_destroy(self.c)
+            self.c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def he_init(seed: int) -> np.ndarray:
+    """Seeded He-normal initial parameters (biases zero) in the flat layout."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for cin, cout in ((2, 32), (32, 32), (32, 32), (32, 1)):
+        out.append(rng.normal(0.0, np.sqrt(2.0 / (9 * cin)), size=cout * cin * 9))
+        out.append(np.zeros(cout))
+    return np.concatenate(out).astype(np.float32)
 
 
 # --------------------------------------------------------- convenience API

@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "fse.h")
 
 def declared_functions():
     src = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:fse_status|const char \*|void)\s*\*?\s*(fse_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:fse_status|const char \*|void|size_t)\s*\*?\s*(fse_\w+)\s*\(",
                                  src, re.M)))
 
 
