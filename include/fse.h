@@ -137,6 +137,33 @@ fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, i
                                  int n_blocks, float *out, float *patches, void *cuda_stream);
 
 /*
+ * Warm start (no counterpart in the paper): Algorithm 1 on the residual of a
+ * caller-supplied estimate e of every block's extrapolation area.  The
+ * support samples become s - e, the model starts at zero, and B receives
+ * e + Re{g}.  init_estimate: device FP32; block i (order of `blocks`) has its
+ * M x M estimate (row-major, sample units, M = b + 2d of its class) at offset
+ * i * est_stride, est_stride >= the largest M*M.  Other arguments as
+ * fse_extrapolate_batch.  The learned initialisation (FSE_INIT_LEARNED) is
+ * this call with e produced on the GPU by the network.
+ */
+fse_status fse_extrapolate_batch_init(fse_handle *h, const void *images, int dtype, int n_images,
+                                      int height, int width, size_t pitch_bytes,
+                                      const uint8_t *loss_mask, const fse_block *blocks,
+                                      int n_blocks, const float *init_estimate, size_t est_stride,
+                                      float *out, float *patches, void *cuda_stream);
+
+/*
+ * Load the learned-initialisation network (FSE_CNN_PARAMS FP32 values, the
+ * layout of fse_cnn_set_params) into a handle created with init =
+ * FSE_INIT_LEARNED (one block class).  fse_extrapolate_batch then, inside its
+ * captured launch, evaluates the network on every block's area (input as
+ * described for the fse_cnn_* calls), runs Algorithm 1 for init_iters (or
+ * iters when 0) iterations on the residual, and writes e + Re{g} on B.
+ * Without loaded weights it returns FSE_ERR_NOT_TRAINED.  Synchronous.
+ */
+fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n);
+
+/*
  * The same computation with HOST buffers (pageable or pinned): copies images
  * and mask to the handle's device staging buffers, runs the batch, copies the
  * patches (layout as above) back, and synchronises the stream before it

@@ -48,6 +48,41 @@ def area_inputs(img: np.ndarray, mask: np.ndarray, x: int, y: int, b: int, d: in
     return s_grid, w_grid, off
 
 
+def cnn_input(img: np.ndarray, mask: np.ndarray, x: int, y: int, b: int, d: int) -> np.ndarray:
+    """Input of the learned-initialisation network for one block: [2, M, M],
+    channel 0 = support sample / 255 (0 off the support), channel 1 = the
+    support indicator (inside the image, not lost, not in the block's B)."""
+    H, W = img.shape
+    M = b + 2 * d
+    ys = np.arange(y - d, y - d + M)
+    xs = np.arange(x - d, x - d + M)
+    inside = ((ys >= 0) & (ys < H))[:, None] & ((xs >= 0) & (xs < W))[None, :]
+    yc = np.clip(ys, 0, H - 1)
+    xc = np.clip(xs, 0, W - 1)
+    s_area = img[np.ix_(yc, xc)].astype(np.float64)
+    own_b = np.zeros((M, M), dtype=bool)
+    own_b[d:d + b, d:d + b] = True
+    sup = inside & (mask[np.ix_(yc, xc)] == 0) & ~own_b
+    return np.stack([np.where(sup, s_area / 255.0, 0.0), sup.astype(np.float64)])
+
+
+def conceal_block_init(img, mask, x, y, cls, est, forced=None):
+    """Warm start: Algorithm 1 on the residual s - est of the support (est:
+    M x M estimate of the area, sample units); returns est + Re{g} on B."""
+    b, d, F, rho, gamma, iters = (cls["block"], cls["border"], cls["fft"], cls["rho"],
+                                  cls["gamma"], cls["iters"])
+    s_grid, w_grid, off = area_inputs(img, mask, x, y, b, d, F, rho)
+    M = b + 2 * d
+    est = np.asarray(est, dtype=np.float64).reshape(M, M)
+    e_grid = np.zeros((F, F))
+    e_grid[off:off + M, off:off + M] = est
+    s_res = np.where(w_grid > 0, s_grid - e_grid, 0.0)
+    res = cfse(s_res, w_grid, gamma, iters, forced=forced)
+    r0 = off + d
+    patch = res.g.real[r0:r0 + b, r0:r0 + b] + est[d:d + b, d:d + b]
+    return patch, res
+
+
 def conceal_block(img, mask, x, y, cls, forced=None):
     """Run the oracle on one block; returns (patch b x b, CfseResult)."""
     b, d, F, rho, gamma, iters = (cls["block"], cls["border"], cls["fft"], cls["rho"],

@@ -72,6 +72,9 @@ def _load():
                                                   vp, vp, vp]
             lib.fse_extrapolate_batch_host.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp,
                                                        c_int, vp, vp]
+            lib.fse_extrapolate_batch_init.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp, c_int,
+                                                       vp, sz, vp, vp, vp]
+            lib.fse_load_init_weights.argtypes = [vp, vp, sz]
             lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
                                                           c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
@@ -80,7 +83,8 @@ def _load():
             lib.fse_destroy.argtypes = [vp]
             lib.fse_destroy.restype = None
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
-                      "fse_extrapolate_batch_noalloc", "fse_get_trace"):
+                      "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_extrapolate_batch_init",
+                      "fse_load_init_weights"):
                 getattr(lib, n).restype = c_int
             fp = ctypes.POINTER(ctypes.c_float)
             lib.fse_cnn_param_count.restype = sz
@@ -128,6 +132,23 @@ def fse_extrapolate_batch(h, images: int, dtype: int, n_images: int, height: int
                                        loss_mask, blocks.ctypes.data if n_blocks else None, n_blocks,
                                        out, patches, stream)
     _check(st, h)
+
+
+def fse_extrapolate_batch_init(h, images: int, dtype: int, n_images: int, height: int, width: int,
+                               pitch_bytes: int, loss_mask: int, blocks: np.ndarray, n_blocks: int,
+                               init_estimate: int, est_stride: int, out: int | None, patches: int | None,
+                               stream: int | None) -> None:
+    """Warm start from caller estimates (device pointer, block i at i * est_stride)."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+    st = _load().fse_extrapolate_batch_init(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask,
+                                            blocks.ctypes.data if n_blocks else None, n_blocks, init_estimate,
+                                            est_stride, out, patches, stream)
+    _check(st, h)
+
+
+def fse_load_init_weights(h, params: np.ndarray) -> None:
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_load().fse_load_init_weights(h, params.ctypes.data, params.size), h)
 
 
 def fse_extrapolate_batch_host(h, images: np.ndarray, dtype: int, n_images: int, height: int,
@@ -288,14 +309,15 @@ def he_init(seed: int) -> np.ndarray:
 
 
 # --------------------------------------------------------- convenience API
-def make_config(classes, device: int = 0, trace: bool = False) -> fse_config:
+def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero",
+                init_iters: int = 0) -> fse_config:
     cfg = fse_config()
     cfg.n_classes = len(classes)
     for i, c in enumerate(classes):
         cfg.cls[i] = fse_class(int(c["block"]), int(c["border"]), int(c["fft"]), float(c["rho"]),
                                float(c["gamma"]), int(c["iters"]))
-    cfg.init = FSE_INIT_ZERO
-    cfg.init_iters = 0
+    cfg.init = FSE_INIT_LEARNED if init == "learned" else FSE_INIT_ZERO
+    cfg.init_iters = int(init_iters)
     cfg.device = device
     cfg.flags = FSE_FLAG_TRACE if trace else 0
     return cfg
@@ -307,10 +329,16 @@ class Engine:
     classes: list of dicts with keys block, border, fft, rho, gamma, iters.
     """
 
-    def __init__(self, classes, device: int = 0, trace: bool = False):
+    def __init__(self, classes, device: int = 0, trace: bool = False, init: str = "zero", init_iters: int = 0,
+                 weights=None):
         self.classes = [dict(c) for c in classes]
-        self.h = fse_create(make_config(classes, device, trace))
+        self.h = fse_create(make_config(classes, device, trace, init, init_iters))
         self.last_n = 0
+        if weights is not None:
+            fse_load_init_weights(self.h, weights)
+
+    def load_init_weights(self, weights):
+        fse_load_init_weights(self.h, weights)
 
     def patch_total(self, blocks) -> int:
         b = np.array([self.classes[int(c)]["block"] for c in np.asarray(blocks).reshape(-1, 4)[:, 3]])
@@ -337,6 +365,23 @@ class Engine:
         fse_extrapolate_batch(self.h, images.data_ptr(), dtype, N, H, W, pitch, mask.data_ptr(), blocks,
                               len(blocks), out.data_ptr() if out is not None else None,
                               patches.data_ptr() if patches is not None else None, stream)
+        self.last_n = len(blocks)
+
+    def run_init(self, images, mask, blocks, est, out=None, patches=None, stream=None) -> None:
+        """Warm start: est is a cuda float32 [n_blocks, M*M] (or wider) tensor of
+        per-block area estimates in sample units."""
+        import torch
+        N, H, W = images.shape
+        dtype = FSE_DTYPE_U8 if images.dtype == torch.uint8 else FSE_DTYPE_F32
+        pitch = images.stride(1) * images.element_size()
+        blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+        assert est.is_cuda and est.dtype == torch.float32 and est.is_contiguous() and est.shape[0] == len(blocks)
+        if stream is None:
+            stream = torch.cuda.current_stream(images.device).cuda_stream
+        fse_extrapolate_batch_init(self.h, images.data_ptr(), dtype, N, H, W, pitch, mask.data_ptr(), blocks,
+                                   len(blocks), est.data_ptr(), est.stride(0),
+                                   out.data_ptr() if out is not None else None,
+                                   patches.data_ptr() if patches is not None else None, stream)
         self.last_n = len(blocks)
 
     def run_host(self, images: np.ndarray, mask: np.ndarray, blocks, patches: np.ndarray = None):

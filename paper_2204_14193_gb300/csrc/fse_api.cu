@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "fse.h"
+#include "fse_cnn.cuh"
 #include "fse_device.cuh"
 
 using fse::BlockRec;
@@ -107,6 +109,19 @@ struct fse_handle {
     size_t mask_cap = 0;
     float *d_patch = nullptr;
     size_t patch_cap = 0;
+    // learned initialisation (FSE_INIT_LEARNED)
+    bool weights_loaded = false;
+    float *d_cnn_params = nullptr;
+    __nv_bfloat16 *d_cnn_wb = nullptr;
+    float *d_cnn_wt = nullptr;
+    int cnn_M = 0;                  // area edge shared by every class
+    int cnn_chunk = 2048;           // areas per CNN pass inside the graph
+    __nv_bfloat16 *d_cnn_x = nullptr, *d_cnn_a0 = nullptr, *d_cnn_a1 = nullptr;
+    float *d_cnn_out = nullptr;
+    float *d_est = nullptr;         // per-block estimates (sample units)
+    size_t est_cap = 0;
+    bool learned_launch = false;   // the captured graph runs the CNN first
+    int learned_n = 0;
     std::string err = "no error";
 };
 
@@ -160,8 +175,12 @@ fse_status validate_config(const fse_config *cfg) {
     }
     if (cfg->init != FSE_INIT_ZERO && cfg->init != FSE_INIT_LEARNED)
         return fail(nullptr, FSE_ERR_INVALID_ARG, "init mode %d unknown", cfg->init);
-    if (cfg->init == FSE_INIT_LEARNED)
-        return fail(nullptr, FSE_ERR_UNSUPPORTED, "learned initialisation is created with fse_create_learned");
+    if (cfg->init == FSE_INIT_LEARNED) {
+        if (cfg->n_classes != 1)
+            return fail(nullptr, FSE_ERR_UNSUPPORTED, "learned initialisation supports one block class per handle");
+        if (cfg->init_iters < 0 || cfg->init_iters > 4096)
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "init_iters %d not in [0, 4096]", cfg->init_iters);
+    }
     if (cfg->flags & ~FSE_FLAG_TRACE) return fail(nullptr, FSE_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
     return FSE_OK;
 }
@@ -271,9 +290,66 @@ fse_status grow(fse_handle *h, T **ptr, size_t *cap, size_t need) {
     return FSE_OK;
 }
 
+// CNN input of the blocks at sorted positions first .. first+count-1: per area
+// sample (M x M, row-major) the pair (support sample / 255, support
+// indicator); support = inside the image, not lost, not in the block's own B
+// (the same test as the concealment kernel's gather).
+__global__ void cnn_gather_kernel(const DevParams P, int first, int count, int M, int d, int b,
+                                  __nv_bfloat162 *__restrict__ xin) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long MM = (long long)M * M;
+    if (i >= count * MM) return;
+    const int q = (int)(i / MM), r = (int)(i % MM), am = r / M, an = r % M;
+    const BlockRec blk = P.blocks[first + q];
+    const int yy = blk.y - d + am, xx = blk.x - d + an;
+    const bool inB = am >= d && am < d + b && an >= d && an < d + b;
+    float sv = 0.f, a = 0.f;
+    if (!inB && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W &&
+        P.mask[((size_t)blk.image * P.H + yy) * P.W + xx] == 0) {
+        const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+        sv = (P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx] : reinterpret_cast<const float *>(row)[xx]) *
+             (1.f / 255.f);
+        a = 1.f;
+    }
+    xin[i] = __floats2bfloat162_rn(sv, a);
+}
+
+// network output (estimate / 255) of those blocks -> per-block estimates in
+// sample units, at the caller's block order
+__global__ void est_scatter_kernel(const float *__restrict__ out, const BlockRec *__restrict__ blocks, int first,
+                                   int count, int MM, float *__restrict__ est, long long stride) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)count * MM) return;
+    const int q = (int)(i / MM);
+    est[blocks[first + q].orig * stride + i % MM] = 255.f * out[i];
+}
+
 fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     FSE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    if (h->learned_launch) {
+        // learned initialisation: CNN over all blocks in chunks, estimates
+        // scattered to h->d_est, then the concealment from the residual
+        const int M = h->cnn_M, MM = M * M;
+        const fse::DevClass &C = h->params.cls[0];
+        for (int first = 0; first < h->learned_n; first += h->cnn_chunk) {
+            const int cnt = std::min(h->cnn_chunk, h->learned_n - first);
+            const long long np = (long long)cnt * MM;
+            cnn_gather_kernel<<<(unsigned)((np + 255) / 256), 256, 0, h->cap_stream>>>(
+                h->params, first, cnt, M, C.d, C.b, reinterpret_cast<__nv_bfloat162 *>(h->d_cnn_x));
+            const unsigned cg = (unsigned)((np + 127) / 128);
+            fse_net::conv_fwd_kernel<0><<<cg, 128, 0, h->cap_stream>>>(h->d_cnn_x, h->d_cnn_wb, h->d_cnn_params,
+                                                                       h->d_cnn_a0, cnt, M, M);
+            fse_net::conv_fwd_kernel<1><<<cg, 128, 0, h->cap_stream>>>(h->d_cnn_a0, h->d_cnn_wb, h->d_cnn_params,
+                                                                       h->d_cnn_a1, cnt, M, M);
+            fse_net::conv_fwd_kernel<2><<<cg, 128, 0, h->cap_stream>>>(h->d_cnn_a1, h->d_cnn_wb, h->d_cnn_params,
+                                                                       h->d_cnn_a0, cnt, M, M);
+            fse_net::conv_fwd_kernel<3><<<cg, 128, 0, h->cap_stream>>>(h->d_cnn_a0, h->d_cnn_wb, h->d_cnn_params,
+                                                                       h->d_cnn_out, cnt, M, M);
+            est_scatter_kernel<<<(unsigned)((np + 255) / 256), 256, 0, h->cap_stream>>>(
+                h->d_cnn_out, h->d_blocks, first, cnt, MM, h->d_est, (long long)MM);
+        }
+    }
     cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
     if (nt == 256)
         fse::fse_batch_kernel<256><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params);
@@ -344,7 +420,10 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
 
 fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
                      size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks, float *out,
-                     float *patches, cudaStream_t stream) {
+                     float *patches, cudaStream_t stream, const float *est = nullptr, long long est_stride = 0) {
+    const bool learned = h->cfg.init == FSE_INIT_LEARNED && est == nullptr;
+    if (learned && n_blocks > 0 && !h->weights_loaded)
+        return fail(h, FSE_ERR_NOT_TRAINED, "learned initialisation: no weights loaded (fse_load_init_weights)");
     if (n_blocks < 0) return fail(h, FSE_ERR_INVALID_ARG, "n_blocks %d < 0", n_blocks);
     if (n_blocks > 0 && !out && !patches) return fail(h, FSE_ERR_INVALID_ARG, "out and patches are both NULL");
     // plan key: every input of the captured launch (block list, pointers, geometry)
@@ -352,7 +431,8 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     if (n_blocks > 0 && blocks) {
         key = hash_words(blocks, (size_t)n_blocks * sizeof(fse_block), 0x51ed270b27a1f3c5ull);
         const uintptr_t ptrs[4] = {(uintptr_t)images, (uintptr_t)mask, (uintptr_t)out, (uintptr_t)patches};
-        const long long geo[6] = {dtype, n_images, height, width, (long long)pitch, n_blocks};
+        const long long geo[8] = {dtype, n_images, height, width, (long long)pitch, n_blocks,
+                                  (long long)(uintptr_t)est, est_stride};
         key = fnv1a(ptrs, sizeof ptrs, key);
         key = fnv1a(geo, sizeof geo, key);
     }
@@ -372,6 +452,7 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     const bool trace = (h->cfg.flags & FSE_FLAG_TRACE) != 0;
     int stride = 0;
     for (int c = 0; c < h->cfg.n_classes; ++c) stride = std::max(stride, h->cfg.cls[c].iters);
+    if (learned && h->cfg.init_iters > 0) stride = h->cfg.init_iters;
     stride = std::max(stride, 1);
 
     if (h->graph_valid) {
@@ -438,7 +519,7 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         D.d = k.border;
         D.M = k.block + 2 * k.border;
         D.off = (k.fft - D.M) / 2;
-        D.iters = k.iters;
+        D.iters = (learned && h->cfg.init_iters > 0) ? h->cfg.init_iters : k.iters;
         D.bpi = 4096 / (k.fft * k.fft);
         D.gamma = k.gamma;
         D.wtab = h->d_wtab[c];
@@ -449,6 +530,25 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     P.tr_coef = trace ? h->d_tr_coef : nullptr;
     P.tr_stride = stride;
     P.tw = h->d_tw;
+    h->learned_launch = learned;
+    h->learned_n = n_blocks;
+    if (learned) {
+        const int MM = h->cnn_M * h->cnn_M;
+        st = grow(h, &h->d_est, &h->est_cap, (size_t)n_blocks * MM);
+        if (st != FSE_OK) return st;
+        if (!h->d_cnn_x) {
+            const size_t C = (size_t)h->cnn_chunk;
+            FSE_CUDA(h, cudaMalloc(&h->d_cnn_x, C * MM * 2 * sizeof(__nv_bfloat16)));
+            FSE_CUDA(h, cudaMalloc(&h->d_cnn_a0, C * MM * 32 * sizeof(__nv_bfloat16)));
+            FSE_CUDA(h, cudaMalloc(&h->d_cnn_a1, C * MM * 32 * sizeof(__nv_bfloat16)));
+            FSE_CUDA(h, cudaMalloc(&h->d_cnn_out, C * MM * sizeof(float)));
+        }
+        P.est = h->d_est;
+        P.est_stride = MM;
+    } else {
+        P.est = est;
+        P.est_stride = est_stride;
+    }
     int nt = 256, cps = h->max_ctas_per_sm_256;
     st = autotune(h, pl, stream, &nt, &cps);
     if (st != FSE_OK) return st;
@@ -479,6 +579,7 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     fse_handle *h = new fse_handle();
     h->cfg = *cfg;
     h->device = cfg->device;
+    h->cnn_M = cfg->cls[0].block + 2 * cfg->cls[0].border;
     auto bail = [&](fse_status s) {
         g_create_error = h->err;
         fse_destroy(h);
@@ -535,6 +636,53 @@ fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, i
     DeviceGuard guard(h->device);
     return run_batch(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks, n_blocks, out,
                      patches, static_cast<cudaStream_t>(cuda_stream));
+}
+
+fse_status fse_extrapolate_batch_init(fse_handle *h, const void *images, int dtype, int n_images, int height,
+                                      int width, size_t pitch_bytes, const uint8_t *loss_mask,
+                                      const fse_block *blocks, int n_blocks, const float *init_estimate,
+                                      size_t est_stride, float *out, float *patches, void *cuda_stream) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (n_blocks > 0 && !init_estimate) return fail(h, FSE_ERR_INVALID_ARG, "init_estimate is NULL");
+    long long maxMM = 0;
+    for (int c = 0; c < h->cfg.n_classes; ++c) {
+        const long long M = h->cfg.cls[c].block + 2 * h->cfg.cls[c].border;
+        maxMM = std::max(maxMM, M * M);
+    }
+    if ((long long)est_stride < maxMM)
+        return fail(h, FSE_ERR_INVALID_ARG, "est_stride %zu < largest area %lld", est_stride, maxMM);
+    DeviceGuard guard(h->device);
+    return run_batch(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks, n_blocks, out,
+                     patches, static_cast<cudaStream_t>(cuda_stream), init_estimate, (long long)est_stride);
+}
+
+fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (h->cfg.init != FSE_INIT_LEARNED)
+        return fail(h, FSE_ERR_INVALID_ARG, "handle was not created with FSE_INIT_LEARNED");
+    if (!params || n != (size_t)fse_net::kParams)
+        return fail(h, FSE_ERR_INVALID_ARG, "need %d parameters", fse_net::kParams);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(params[i])) return fail(h, FSE_ERR_INVALID_ARG, "parameter %zu is not finite", i);
+    DeviceGuard guard(h->device);
+    if (!h->d_cnn_params) {
+        FSE_CUDA(h, cudaMalloc(&h->d_cnn_params, fse_net::kParams * sizeof(float)));
+        FSE_CUDA(h, cudaMalloc(&h->d_cnn_wb, fse_net::kWbTotal * sizeof(__nv_bfloat16)));
+        FSE_CUDA(h, cudaMalloc(&h->d_cnn_wt, fse_net::kWtTotal * sizeof(float)));
+    }
+    FSE_CUDA(h, cudaDeviceSynchronize());
+    FSE_CUDA(h, cudaMemcpy(h->d_cnn_params, params, n * sizeof(float), cudaMemcpyHostToDevice));
+    const int m = std::max(fse_net::kWbTotal, fse_net::kWtTotal);
+    fse_net::pack_weights_kernel<<<(m + 255) / 256, 256>>>(h->d_cnn_params, h->d_cnn_wb, h->d_cnn_wt);
+    FSE_CUDA(h, cudaGetLastError());
+    FSE_CUDA(h, cudaDeviceSynchronize());
+    h->weights_loaded = true;
+    h->graph_valid = false;   // the captured launch reads the new weights anyway; re-plan to be safe
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return FSE_OK;
 }
 
 fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dtype, int n_images, int height,
@@ -607,6 +755,14 @@ void fse_destroy(fse_handle *h) {
         cudaFree(h->d_img);
         cudaFree(h->d_mask);
         cudaFree(h->d_patch);
+        cudaFree(h->d_cnn_params);
+        cudaFree(h->d_cnn_wb);
+        cudaFree(h->d_cnn_wt);
+        cudaFree(h->d_cnn_x);
+        cudaFree(h->d_cnn_a0);
+        cudaFree(h->d_cnn_a1);
+        cudaFree(h->d_cnn_out);
+        cudaFree(h->d_est);
         if (h->upload_done) cudaEventDestroy(h->upload_done);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     }

@@ -40,7 +40,7 @@ static_assert(woff_of(kLayers) == kParams, "parameter count");
 
 // ---------------------------------------------------------------- weights
 // Flat FP32 parameters -> forward B operands (bf16) and backward weights.
-__global__ void pack_weights_kernel(const float *__restrict__ params, __nv_bfloat16 *__restrict__ wb,
+static __global__ void pack_weights_kernel(const float *__restrict__ params, __nv_bfloat16 *__restrict__ wb,
                                     float *__restrict__ wt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     // forward operands
@@ -67,7 +67,7 @@ __global__ void pack_weights_kernel(const float *__restrict__ params, __nv_bfloa
 }
 
 // FP32 NCHW input [N][2][H][W] -> bf16 NHWC [N*H*W][2]
-__global__ void input_kernel(const float *__restrict__ x, __nv_bfloat162 *__restrict__ xin, int N, int HW) {
+static __global__ void input_kernel(const float *__restrict__ x, __nv_bfloat162 *__restrict__ xin, int N, int HW) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (long long)N * HW) return;
     const long long n = p / HW, r = p % HW;
@@ -75,7 +75,7 @@ __global__ void input_kernel(const float *__restrict__ x, __nv_bfloat162 *__rest
 }
 
 // ---------------------------------------------------------------- forward
-__device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, uint32_t b0, uint32_t b1) {
+static __device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const __nv_bfloat16 *__re
 
 // --------------------------------------------------------------- backward
 // dL/dout = 2 lam (out - t) / count; per-CTA partial loss sums (256 threads).
-__global__ void out_grad_kernel(const float *__restrict__ y, const float *__restrict__ t,
+static __global__ void out_grad_kernel(const float *__restrict__ y, const float *__restrict__ t,
                                 const float *__restrict__ lam, float *__restrict__ gy, double *__restrict__ lpart,
                                 long long P, float scale) {
     __shared__ double red[256];
@@ -306,7 +306,7 @@ __global__ void reduce_grad_kernel(const float *__restrict__ part, int nparts, f
     grad[dst] = (float)s;
 }
 
-__global__ void sum_loss_kernel(const double *__restrict__ lpart, int n, double *__restrict__ out, double inv) {
+static __global__ void sum_loss_kernel(const double *__restrict__ lpart, int n, double *__restrict__ out, double inv) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += lpart[i];
@@ -314,7 +314,7 @@ __global__ void sum_loss_kernel(const double *__restrict__ lpart, int n, double 
 }
 
 // Adam with bias correction on the FP32 master parameters.
-__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+static __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                             const float *__restrict__ g, int n, float lr, float b1, float b2, float eps,
                             float c1, float c2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

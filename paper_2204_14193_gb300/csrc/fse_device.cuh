@@ -63,6 +63,8 @@ struct DevParams {
     float2 *tr_coef;
     int tr_stride;
     const float2 *tw;                 // 64 entries (cos, sin)(2 pi t / 64)
+    const float *est;                 // warm start: per-block estimate (sample units) or nullptr
+    long long est_stride;             // floats between two blocks' estimates (block order: orig)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -415,8 +417,10 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
                          !(am >= d && am < d + b && an >= d && an < d + b) &&
                          yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0;
         const float w = inA ? __ldg(&C.wtab[am * M + an]) : 0.f;
-        const float ws = w * sv[t];
-        sws2 = fmaf(ws, sv[t], sws2);
+        // warm start: the support holds the residual of the estimate
+        const float sr = (inA && P.est != nullptr) ? sv[t] - P.est[blk.orig * P.est_stride + am * M + an] : sv[t];
+        const float ws = w * sr;
+        sws2 = fmaf(ws, sr, sws2);
         sw += w;
         Z[m * FP + n] = make_float2(ws, w);
     }
@@ -578,9 +582,10 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         const int j = lt + t * TB;
         if (j < b * b) {
             const int pm = j / b, pn = j % b;
-            if (P.out != nullptr)
-                P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = acc[t];
-            if (P.patches != nullptr) P.patches[blk.patch_off + j] = acc[t];
+            const float val =
+                acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
+            if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
+            if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
         }
     }
 }

@@ -172,3 +172,24 @@ def loss_mask(blocks: np.ndarray, sizes, n_images: int, H: int, W: int) -> np.nd
         b = sizes[int(c)]
         m[int(im), int(y):int(y) + b, int(x):int(x) + b] = 1
     return m
+
+
+def noisy_estimates(seed: int, images: np.ndarray, blocks: np.ndarray, classes, sigma: float = 8.0,
+                    stride: int | None = None) -> np.ndarray:
+    """Seeded stand-ins for an initial estimate of each block's area: the
+    unlost image over the area (edge-clamped outside the image) plus Gaussian
+    noise of standard deviation sigma.  Returns float32 [n_blocks, stride]
+    (area row-major in the first M*M entries)."""
+    rng = np.random.default_rng(seed)
+    blocks = np.asarray(blocks).reshape(-1, 4)
+    Ms = [c["block"] + 2 * c["border"] for c in classes]
+    stride = stride or max(M * M for M in Ms)
+    est = np.zeros((len(blocks), stride), np.float32)
+    for i, (im, x, y, c) in enumerate(blocks):
+        d, M = classes[c]["border"], Ms[c]
+        H, W = images.shape[1:]
+        ys = np.clip(np.arange(y - d, y - d + M), 0, H - 1)
+        xs = np.clip(np.arange(x - d, x - d + M), 0, W - 1)
+        a = images[im][np.ix_(ys, xs)].astype(np.float64) + rng.normal(0.0, sigma, (M, M))
+        est[i, :M * M] = a.ravel()
+    return est

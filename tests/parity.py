@@ -37,21 +37,32 @@ def mirror(sel, F):
     return ((-(sel // F)) % F) * F + ((-(sel % F)) % F)
 
 
-def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None):
+def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, est=None, iters=None):
     """Compare one block.  Returns a dict of diagnostics; raises nothing.
-    gpu_sel / gpu_energy: the kernel's selection trace and FP32 energies."""
+    gpu_sel / gpu_energy: the kernel's selection trace and FP32 energies.
+    est: warm start, the M x M area estimate (the model then starts from the
+    residual s - est on the support and the output is est + Re{g} on B).
+    iters: iteration count in place of the class's."""
     im, x, y, c = (int(v) for v in blk)
     k = cls[c]
-    F, b, I = k["fft"], k["block"], k["iters"]
+    F, b, I = k["fft"], k["block"], k["iters"] if iters is None else iters
     s_grid, w_grid, off = oimage.area_inputs(img, mask, x, y, b, k["border"], F, k["rho"])
+    est_b = 0.0
+    if est is not None:
+        M = b + 2 * k["border"]
+        est = np.asarray(est, dtype=np.float64).reshape(M, M)
+        e_grid = np.zeros((F, F))
+        e_grid[off:off + M, off:off + M] = est
+        s_grid = np.where(w_grid > 0, s_grid - e_grid, 0.0)
+        est_b = est[k["border"]:k["border"] + b, k["border"]:k["border"] + b]
     out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False,
                max_delta=0.0, widened=False)
     free = oracle.cfse(s_grid, w_grid, k["gamma"], I)
     r0 = off + k["border"]
-    free_patch = free.g.real[r0:r0 + b, r0:r0 + b]
+    free_patch = free.g.real[r0:r0 + b, r0:r0 + b] + est_b
     if gpu_sel is None:
         # no trace: only the free run can be compared
-        out["max_pix"] = float(np.max(np.abs(free_patch - gpu_patch))) if I else float(np.max(np.abs(gpu_patch)))
+        out["max_pix"] = float(np.max(np.abs(free_patch - gpu_patch)))
         out["ok"] = out["max_pix"] <= PIX_TOL
         return out
     gsel = np.asarray(gpu_sel[:I], dtype=np.int64)
@@ -83,16 +94,17 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None):
         if np.any(1.0 - ratio > band) or out["max_delta"] > DELTA_MAX:
             out["ok"] = False
         out["widened"] = bool(np.any(1.0 - ratio > EPS_TIE))
-    gp = guided.g.real[r0:r0 + b, r0:r0 + b]
+    gp = guided.g.real[r0:r0 + b, r0:r0 + b] + est_b
     out["max_pix"] = float(np.max(np.abs(gp - gpu_patch)))
     if out["max_pix"] > PIX_TOL:
         out["ok"] = False
     return out
 
 
-def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None):
+def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None, ests=None, iters=None):
     """Check every block of a batch; patches is the flat patch array (caller
-    order), sels / energies the [n, stride] trace or None."""
+    order), sels / energies the [n, stride] trace or None, ests the per-block
+    warm-start estimates [n, >= M*M] or None."""
     blocks = np.asarray(blocks).reshape(-1, 4)
     offs = np.zeros(len(blocks) + 1, np.int64)
     for i, bk in enumerate(blocks):
@@ -105,7 +117,9 @@ def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, th
         p = np.asarray(patches[offs[i]:offs[i + 1]], dtype=np.float64).reshape(b, b)
         return check_block(images[int(bk[0])], mask[int(bk[0])], bk, cls, p,
                            None if sels is None else sels[i],
-                           None if energies is None else energies[i])
+                           None if energies is None else energies[i],
+                           None if ests is None else ests[i][:(b + 2 * cls[int(bk[3])]["border"]) ** 2],
+                           iters)
 
     n = threads or len(os.sched_getaffinity(0))
     with ThreadPoolExecutor(max_workers=n) as ex:

@@ -68,3 +68,11 @@ def test_null_handle_is_rejected():
     st = P._load().fse_extrapolate_batch(None, None, 0, 1, 1, 1, 1, None, None, 0, None, None, None)
     assert st == 1
     P.fse_destroy(None)
+
+
+@pytest.mark.parametrize("n_classes,init_iters,status", [(2, 10, 2), (1, -1, 1), (1, 5000, 1)])
+def test_learned_config_validation(n_classes, init_iters, status):
+    cls = dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=10)
+    with pytest.raises(P.FseError) as ei:
+        P.fse_create(P.make_config([cls] * n_classes, init="learned", init_iters=init_iters))
+    assert ei.value.status == status
