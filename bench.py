@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--init-iters", type=int, default=50)
     return ap.parse_args()
 
 
@@ -59,14 +61,16 @@ def workload(rank: int, frames: int, device):
     import torch
     from paper_2204_14193_gb300 import synth
     vid = synth.make_video_torch(2022 + rank, frames, H, W, device=device)
-    blocks = np.concatenate([synth.grid_losses(100_000 * (rank + 1) + t, H, W, 16, LOSS, image=t)
-                             for t in range(frames)])
-    cells = torch.zeros((frames, H // 16, W // 16), dtype=torch.uint8)
-    bt = torch.from_numpy(blocks.astype(np.int64))
-    cells[bt[:, 0], bt[:, 2] // 16, bt[:, 1] // 16] = 1
-    mask = torch.zeros((frames, H, W), dtype=torch.uint8, device=device)
-    mask[:, :(H // 16) * 16, :] = cells.to(device).repeat_interleave(16, 1).repeat_interleave(16, 2)
+    blocks = workload_blocks(rank, frames)
+    mask = synth.grid_mask_torch(blocks, 16, frames, H, W, device=device)
     return vid, mask, blocks
+
+
+def workload_blocks(rank: int, frames: int) -> np.ndarray:
+    """The lost blocks of a rank's batch (seeds differ per rank and frame)."""
+    from paper_2204_14193_gb300 import synth
+    return np.concatenate([synth.grid_losses(100_000 * (rank + 1) + t, H, W, 16, LOSS, image=t)
+                           for t in range(frames)])
 
 
 class ClockSampler:
@@ -178,6 +182,65 @@ def cpu_oracle_rate(frames_host, mask_host, blocks, seconds: float, seed: int = 
     return done / dt, cores, done
 
 
+def job_throughput(ms_local: float, units_local: int, device):
+    """Whole-job figures under weak scaling: every rank processes its own
+    units (no collective on the data path); the step time is the maximum over
+    ranks and the units are summed.  Returns (ms_max, units_total, units/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max, units = float(t.item()), float(u.item())
+    return ms_max, units, units / (ms_max / 1e3)
+
+
+def timed_runs(eng, vid, mask, blocks, patches, steps, warmup, stream, dev):
+    import torch
+    for _ in range(warmup):
+        eng.run(vid, mask, blocks, patches=patches)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        eng.run(vid, mask, blocks, patches=patches)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def learned_leg(P, vid, mask, blocks, plain_patches, args, stream, dev):
+    """Learned initialisation (network, then init_iters iterations on the
+    residual) against plain extrapolation at I=200 and at init_iters, on the
+    same batch: blocks/s and PSNR of the lost samples against the frames."""
+    import torch
+    from paper_2204_14193_gb300 import train_init
+    try:
+        w = train_init.load_weights()
+    except (OSError, ValueError) as e:
+        return {"available": False, "why": str(e)}
+    n = len(blocks)
+    truth = train_init.truth_patches(vid, blocks)
+    ps = lambda p: train_init.psnr(p.view(n, 16, 16), truth)  # noqa: E731
+    out = {"init_iters": args.init_iters, "plain_i200_psnr_db": ps(plain_patches)}
+    k = max(3, min(args.steps, 10))
+    eng = P.Engine([CLS], init="learned", init_iters=args.init_iters, weights=w)
+    pl = torch.empty_like(plain_patches)
+    ms = timed_runs(eng, vid, mask, blocks, pl, k, max(args.warmup, 2), stream, dev)
+    eng.close()
+    out.update(value=n / (ms / 1e3), unit="blocks/s", ms_per_step=ms, psnr_db=ps(pl))
+    eng = P.Engine([dict(CLS, iters=args.init_iters)])
+    ms_p = timed_runs(eng, vid, mask, blocks, pl, k, max(args.warmup, 2), stream, dev)
+    eng.close()
+    out.update({f"plain_i{args.init_iters}_blocks_per_s": n / (ms_p / 1e3),
+                f"plain_i{args.init_iters}_psnr_db": ps(pl),
+                "network_ms_per_step_est": ms - ms_p,
+                "weights": os.path.relpath(train_init.weights_path(), ROOT)})
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -267,11 +330,7 @@ def main():
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n_blocks * world / (ms_max / 1e3)
+    ms_max, _units, value = job_throughput(ms, n_blocks, dev)
     clocks = clk.summary()
 
     # ---- end to end through the host-buffer entry point ----
@@ -288,15 +347,17 @@ def main():
         for _ in range(k):
             eng.run_host(h_vid, h_mask, blocks, h_patch)
         dt = (time.perf_counter() - t0) / k
-        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": n_blocks * world / dt, "unit": "blocks/s",
+        dt_ms, _units, e2e_value = job_throughput(dt * 1e3, n_blocks, dev)
+        dt = dt_ms / 1e3
+        e2e = {"value": e2e_value, "unit": "blocks/s",
                "h2d_bytes_per_step": int(h_vid.nbytes + h_mask.nbytes + blocks.nbytes),
                "d2h_bytes_per_step": int(h_patch.nbytes), "ms_per_step": dt * 1e3}
         # the e2e patches equal the device-path patches bit for bit
         assert np.array_equal(h_patch, patches.cpu().numpy()), "host entry point disagrees with device path"
+
+    learned = None
+    if not args.no_learned and args.iters == 200:
+        learned = learned_leg(P, vid, mask, blocks, patches, args, stream, dev)
 
     # ---- roofline of the persistent kernel (shared-memory bound) ----
     props = torch.cuda.get_device_properties(dev)
@@ -338,9 +399,10 @@ def main():
                                        f"({n_blocks} blocks per GPU), 48x48 areas, F=64, rho 0.8, "
                                        f"gamma 0.5, I={I}, plain (zero) initialisation",
                            "parallelism": f"replicas x{world}", "blocks_per_gpu": n_blocks,
-                           "l2": "inputs larger than L2 (frames + mask > 1 GB per GPU)"},
+                           "l2": f"inputs larger than L2 (frames + mask = {2 * frames * H * W / 1e6:.0f} MB per GPU, "
+                                 "L2 129 MB)"},
                 "clocks": clocks, "gpu_launches": args.steps, "roofline": roofline,
-                "e2e": e2e, "cpu_baseline": cpu}
+                "e2e": e2e, "cpu_baseline": cpu, "learned_init": learned}
         print(json.dumps(line))
     eng.close()
     if world > 1:

@@ -188,6 +188,18 @@ fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dty
 fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef,
                          size_t cap, int *stride_out);
 
+/* The model over every lost block's whole extrapolation area, for the last
+ * batch of a handle created with FSE_FLAG_TRACE: Re{g}[m][n] for the M x M
+ * area, the inverse transform of the accumulated model spectrum G of
+ * Algorithm 1 (Section III: the model g is defined on the whole area L)
+ * evaluated at the area's positions in the F x F grid.  Only the model: a
+ * warm start's estimate is not added.  model: device, block i (caller order)
+ * at model + i * model_stride, row-major, model_stride >= the largest M * M.
+ * Enqueued on cuda_stream (after the last launch's stream has finished when
+ * the two differ); the B samples equal the concealed output bit for bit.
+ * Errors: FSE_ERR_INVALID_ARG (no trace flag, NULL model, short stride). */
+fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, void *cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Learned initialisation network (no counterpart in the paper).
  *

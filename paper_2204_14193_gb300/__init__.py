@@ -75,6 +75,7 @@ def _load():
             lib.fse_extrapolate_batch_init.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp, c_int,
                                                        vp, sz, vp, vp, vp]
             lib.fse_load_init_weights.argtypes = [vp, vp, sz]
+            lib.fse_get_area_model.argtypes = [vp, vp, sz, vp]
             lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
                                                           c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
@@ -84,7 +85,7 @@ def _load():
             lib.fse_destroy.restype = None
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
                       "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_extrapolate_batch_init",
-                      "fse_load_init_weights"):
+                      "fse_load_init_weights", "fse_get_area_model"):
                 getattr(lib, n).restype = c_int
             fp = ctypes.POINTER(ctypes.c_float)
             lib.fse_cnn_param_count.restype = sz
@@ -195,6 +196,10 @@ def fse_get_trace(h, n_blocks: int):
     s = stride.value
     return (sel[:n].reshape(n_blocks, s), en[:n].reshape(n_blocks, s),
             (co[0:2 * n:2] + 1j * co[1:2 * n:2]).astype(np.complex64).reshape(n_blocks, s))
+
+
+def fse_get_area_model(h, model: int, model_stride: int, stream: int | None) -> None:
+    _check(_load().fse_get_area_model(h, model, model_stride, stream), h)
 
 
 def fse_destroy(h) -> None:
@@ -401,6 +406,17 @@ class Engine:
 
     def trace(self):
         return fse_get_trace(self.h, self.last_n)
+
+    def area_model(self, stream=None):
+        """Re{g} over every block's M x M area of the last batch (trace
+        handles only): cuda float32 [n_blocks, max M*M]."""
+        import torch
+        mm = max((c["block"] + 2 * c["border"]) ** 2 for c in self.classes)
+        out = torch.zeros((self.last_n, mm), dtype=torch.float32, device="cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        fse_get_area_model(self.h, out.data_ptr() if self.last_n else None, mm, stream)
+        return out
 
     def close(self):
         if self.h is not None:

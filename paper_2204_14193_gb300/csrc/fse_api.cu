@@ -324,6 +324,51 @@ __global__ void est_scatter_kernel(const float *__restrict__ out, const BlockRec
     est[blocks[first + q].orig * stride + i % MM] = 255.f * out[i];
 }
 
+// Model over the whole extrapolation area from the trace of the last launch:
+// Re{g}[m, n] = Re{sum_i c_i exp(j 2 pi (u_i m + v_i n) / F)} at the area's
+// grid positions (the IFFT of the accumulated model spectrum, Algorithm 1),
+// evaluated with the same operation sequence and twiddle table as the
+// kernel's own evaluation on B, so the B samples agree bit for bit.  One CTA
+// per block (sorted order), 256 threads, up to 9 samples each (M <= 48).
+__global__ void __launch_bounds__(256) area_model_kernel(const DevParams P, float *__restrict__ model,
+                                                         long long mstride) {
+    __shared__ float2 s_tw[64];
+    if (threadIdx.x < 64) s_tw[threadIdx.x] = P.tw[threadIdx.x];
+    __syncthreads();
+    const int q = blockIdx.x;
+    int sg = 0;
+    while (sg + 1 < P.n_seg && q >= P.seg_block_start[sg] + P.seg_block_count[sg]) ++sg;
+    const fse::DevClass &C = P.cls[P.seg_cls[sg]];
+    const BlockRec blk = P.blocks[q];
+    const int F = C.F, M = C.M, MM = M * M, step = 64 / F;
+    constexpr int kPer = 9;
+    float acc[kPer];
+    int pm[kPer], pn[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+        const int p = threadIdx.x + t * 256;
+        acc[t] = 0.f;
+        pm[t] = C.off + p / M;
+        pn[t] = C.off + p % M;
+    }
+    const size_t o = (size_t)blk.orig * P.tr_stride;
+    for (int i = 0; i < C.iters; ++i) {
+        const int sel = P.tr_sel[o + i];
+        const float2 c = P.tr_coef[o + i];
+        const int u = sel / F, v = sel % F;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const float2 tw = s_tw[((u * pm[t] + v * pn[t]) & (F - 1)) * step];
+            acc[t] = fmaf(c.x, tw.x, fmaf(-c.y, tw.y, acc[t]));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+        const int p = threadIdx.x + t * 256;
+        if (p < MM) model[blk.orig * mstride + p] = acc[t];
+    }
+}
+
 fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     FSE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -733,6 +778,25 @@ fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef
     if (sel) FSE_CUDA(h, cudaMemcpy(sel, h->d_tr_sel, n * sizeof(int), cudaMemcpyDeviceToHost));
     if (energy) FSE_CUDA(h, cudaMemcpy(energy, h->d_tr_energy, n * sizeof(float), cudaMemcpyDeviceToHost));
     if (coef) FSE_CUDA(h, cudaMemcpy(coef, h->d_tr_coef, n * sizeof(float2), cudaMemcpyDeviceToHost));
+    return FSE_OK;
+}
+
+fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, void *cuda_stream) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (!(h->cfg.flags & FSE_FLAG_TRACE)) return fail(h, FSE_ERR_INVALID_ARG, "handle was created without FSE_FLAG_TRACE");
+    size_t maxMM = 0;
+    for (int c = 0; c < h->cfg.n_classes; ++c) {
+        const size_t M = (size_t)(h->cfg.cls[c].block + 2 * h->cfg.cls[c].border);
+        maxMM = std::max(maxMM, M * M);
+    }
+    if (model_stride < maxMM) return fail(h, FSE_ERR_INVALID_ARG, "model_stride %zu < largest area %zu", model_stride, maxMM);
+    if (h->last_n_blocks == 0) return FSE_OK;
+    if (!model) return fail(h, FSE_ERR_INVALID_ARG, "model is NULL");
+    DeviceGuard guard(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (st != h->last_stream) FSE_CUDA(h, cudaStreamSynchronize(h->last_stream));
+    area_model_kernel<<<h->last_n_blocks, 256, 0, st>>>(h->params, model, (long long)model_stride);
+    FSE_CUDA(h, cudaGetLastError());
     return FSE_OK;
 }
 

@@ -193,3 +193,13 @@ def noisy_estimates(seed: int, images: np.ndarray, blocks: np.ndarray, classes, 
         a = images[im][np.ix_(ys, xs)].astype(np.float64) + rng.normal(0.0, sigma, (M, M))
         est[i, :M * M] = a.ravel()
     return est
+
+
+def grid_mask_torch(blocks: np.ndarray, b: int, n_images: int, H: int, W: int, device="cuda"):
+    """Loss mask [N, H, W] uint8 on ``device`` for b-aligned grid blocks."""
+    import torch
+    cells = torch.zeros((n_images, (H + b - 1) // b, (W + b - 1) // b), dtype=torch.uint8)
+    bt = torch.from_numpy(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
+    cells[bt[:, 0], bt[:, 2] // b, bt[:, 1] // b] = 1
+    full = cells.to(device).repeat_interleave(b, 1).repeat_interleave(b, 2)
+    return full[:, :H, :W].contiguous()

@@ -241,3 +241,45 @@ def test_full_size_throughput_config_sampled(fse):
     s = parity.summarize(out)
     print("full-size sample:", s)
     assert s["ok"], s
+
+
+# ------------------------------------------------- model over the whole area
+@pytest.mark.parametrize("uneven", [False, True])
+def test_area_model_matches_guided_oracle(fse, uneven):
+    """fse_get_area_model: Re{g} over the whole M x M area equals the oracle's
+    model replayed along the GPU's selections; its B samples are the
+    concealed output bit for bit."""
+    if uneven:
+        img = synth.make_image(53, 256, 256)[None]
+        blocks = synth.uneven_losses(54, 256, 256)
+        cls = [dict(C16, iters=60), dict(C32, iters=90), dict(C64, iters=120)]
+        mask = synth.loss_mask(blocks, [4, 8, 16], 1, 256, 256)
+    else:
+        img = synth.make_image(51, 192, 192)[None]
+        blocks = synth.grid_losses(52, 192, 192, 16, 0.2, non_adjacent=True)
+        cls = [dict(C64, iters=120)]
+        mask = synth.loss_mask(blocks, [16], 1, 192, 192)
+    eng = fse.Engine(cls, trace=True)
+    n = eng.patch_total(blocks)
+    patches = torch.zeros(n, dtype=torch.float32, device="cuda")
+    eng.run(torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda(), blocks, patches=patches)
+    model = eng.area_model().cpu().numpy()
+    sel, energy, _ = eng.trace()
+    eng.close()
+    patches = patches.cpu().numpy()
+    assert_parity(img, mask, blocks, cls, patches, (sel, energy))
+    worst = 0.0
+    off_p = 0
+    for i, (im, x, y, c) in enumerate(blocks):
+        k = cls[int(c)]
+        b, d, F, I = k["block"], k["border"], k["fft"], k["iters"]
+        M = b + 2 * d
+        s_grid, w_grid, off = oimage.area_inputs(img[0], mask[0], int(x), int(y), b, d, F, k["rho"])
+        guided = oracle.cfse(s_grid, w_grid, k["gamma"], I, forced=sel[i, :I].astype(np.int32))
+        ref = guided.g.real[off:off + M, off:off + M]
+        got = model[i, :M * M].reshape(M, M)
+        worst = max(worst, float(np.abs(got - ref).max()))
+        np.testing.assert_array_equal(got[d:d + b, d:d + b].ravel(), patches[off_p:off_p + b * b])
+        off_p += b * b
+    print("area model: worst |gpu - oracle|", worst)
+    assert worst <= parity.PIX_TOL
