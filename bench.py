@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the I sweep and the uneven-size batch")
     ap.add_argument("--init-iters", type=int, default=50)
     return ap.parse_args()
 
@@ -241,6 +242,44 @@ def learned_leg(P, vid, mask, blocks, plain_patches, args, stream, dev):
     return out
 
 
+def iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, peak_gbs):
+    """Plain extrapolation of the same batch at I = 50 and I = 500."""
+    out = {}
+    n = len(blocks)
+    for I in (50, 500):
+        eng = P.Engine([dict(CLS, iters=I)])
+        ms = timed_runs(eng, vid, mask, blocks, patches, 3, 2, stream, dev)
+        eng.close()
+        achieved = n * 8.0 * (I - 1) * CLS["fft"] ** 2 / (ms / 1e3) / 1e9
+        out[f"i{I}"] = {"value": n / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms,
+                        "smem_frac": achieved / peak_gbs}
+    return out
+
+
+def uneven_batch(P, args, stream, dev):
+    """30 frames of 1920x1080 u8 video, 3% of the samples lost in mixed
+    4x4 / 8x8 / 16x16 blocks (borders 6/12/16, FFT 16/32/64), I = 200, one
+    launch over all sizes."""
+    import torch
+    from paper_2204_14193_gb300 import synth
+    T3, H3, W3 = 30, 1080, 1920
+    vid = synth.make_video_torch(3030, T3, H3, W3, device=dev)
+    blocks = np.concatenate([synth.uneven_losses(5000 + t, H3, W3, image=t) for t in range(T3)])
+    mask = torch.from_numpy(synth.loss_mask(blocks, [4, 8, 16], T3, H3, W3)).to(dev)
+    classes = [dict(block=4, border=6, fft=16, rho=0.8, gamma=0.5, iters=200),
+               dict(block=8, border=12, fft=32, rho=0.8, gamma=0.5, iters=200),
+               dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=200)]
+    eng = P.Engine(classes)
+    pt = torch.empty(eng.patch_total(blocks), dtype=torch.float32, device=dev)
+    ms = timed_runs(eng, vid, mask, blocks, pt, 5, 3, stream, dev)
+    eng.close()
+    counts = np.bincount(blocks[:, 3], minlength=3)
+    return {"value": len(blocks) / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms,
+            "workload": f"{T3} x {W3}x{H3} u8 frames, 3% of samples lost in 4/8/16 blocks "
+                        f"({counts[0]}/{counts[1]}/{counts[2]}), F 16/32/64, I=200, one launch",
+            "blocks": int(len(blocks))}
+
+
 def run_reference(args):
     """The oracle as the reference arm (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -358,6 +397,13 @@ def main():
     learned = None
     if not args.no_learned and args.iters == 200:
         learned = learned_leg(P, vid, mask, blocks, patches, args, stream, dev)
+    props0 = torch.cuda.get_device_properties(dev)
+    sm_mhz0 = clocks["sm_mhz"] or clocks["sm_max_mhz"] or max_sm_clock_mhz(local)
+    peak0 = props0.multi_processor_count * 128.0 * sm_mhz0 * 1e6 / 1e9
+    sweep = uneven = None
+    if not args.no_extra and args.iters == 200:
+        sweep = iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, peak0)
+        uneven = uneven_batch(P, args, stream, dev)
 
     # ---- roofline of the persistent kernel (shared-memory bound) ----
     props = torch.cuda.get_device_properties(dev)
@@ -402,7 +448,8 @@ def main():
                            "l2": f"inputs larger than L2 (frames + mask = {2 * frames * H * W / 1e6:.0f} MB per GPU, "
                                  "L2 129 MB)"},
                 "clocks": clocks, "gpu_launches": args.steps, "roofline": roofline,
-                "e2e": e2e, "cpu_baseline": cpu, "learned_init": learned}
+                "e2e": e2e, "cpu_baseline": cpu, "learned_init": learned, "iteration_sweep": sweep,
+                "uneven_batch": uneven}
         print(json.dumps(line))
     eng.close()
     if world > 1:

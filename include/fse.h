@@ -157,8 +157,11 @@ fse_status fse_extrapolate_batch_init(fse_handle *h, const void *images, int dty
  * layout of fse_cnn_set_params) into a handle created with init =
  * FSE_INIT_LEARNED (one block class).  fse_extrapolate_batch then, inside its
  * captured launch, evaluates the network on every block's area (input as
- * described for the fse_cnn_* calls), runs Algorithm 1 for init_iters (or
- * iters when 0) iterations on the residual, and writes e + Re{g} on B.
+ * described for the fse_cnn_* calls), takes its output on B as the estimate
+ * e (zero on the rest of the area, so the support is unchanged), runs
+ * Algorithm 1 for init_iters (or iters when 0) iterations, and writes
+ * e + Re{g} on B: the network is trained to supply what iterations beyond
+ * init_iters would add.
  * Without loaded weights it returns FSE_ERR_NOT_TRAINED.  Synchronous.
  */
 fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n);
@@ -199,6 +202,13 @@ fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef
  * the two differ); the B samples equal the concealed output bit for bit.
  * Errors: FSE_ERR_INVALID_ARG (no trace flag, NULL model, short stride). */
 fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, void *cuda_stream);
+
+/* Wait for the handle's last launch and report device-side failures: the
+ * learned-initialisation kernel bounds every wait on its tensor-core work
+ * (1 s) and, when one expires, records it, frees its tensor memory and
+ * stops; fse_sync then returns FSE_ERR_TIMEOUT (and clears the record).
+ * No counterpart in the paper. */
+fse_status fse_sync(fse_handle *h);
 
 /* ------------------------------------------------------------------------
  * Learned initialisation network (no counterpart in the paper).

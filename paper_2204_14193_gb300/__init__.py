@@ -76,6 +76,7 @@ def _load():
                                                        vp, sz, vp, vp, vp]
             lib.fse_load_init_weights.argtypes = [vp, vp, sz]
             lib.fse_get_area_model.argtypes = [vp, vp, sz, vp]
+            lib.fse_sync.argtypes = [vp]
             lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
                                                           c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
@@ -85,7 +86,7 @@ def _load():
             lib.fse_destroy.restype = None
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
                       "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_extrapolate_batch_init",
-                      "fse_load_init_weights", "fse_get_area_model"):
+                      "fse_load_init_weights", "fse_get_area_model", "fse_sync"):
                 getattr(lib, n).restype = c_int
             fp = ctypes.POINTER(ctypes.c_float)
             lib.fse_cnn_param_count.restype = sz
@@ -200,6 +201,10 @@ def fse_get_trace(h, n_blocks: int):
 
 def fse_get_area_model(h, model: int, model_stride: int, stream: int | None) -> None:
     _check(_load().fse_get_area_model(h, model, model_stride, stream), h)
+
+
+def fse_sync(h) -> None:
+    _check(_load().fse_sync(h), h)
 
 
 def fse_destroy(h) -> None:
@@ -406,6 +411,11 @@ class Engine:
 
     def trace(self):
         return fse_get_trace(self.h, self.last_n)
+
+    def sync(self):
+        """Wait for the last launch; raises FseError(FSE_ERR_TIMEOUT) when a
+        bounded device-side wait expired."""
+        fse_sync(self.h)
 
     def area_model(self, stream=None):
         """Re{g} over every block's M x M area of the last batch (trace

@@ -19,6 +19,7 @@
 
 #include "fse.h"
 #include "fse_cnn.cuh"
+#include "fse_cnn_tc.cuh"
 #include "fse_device.cuh"
 
 using fse::BlockRec;
@@ -122,6 +123,9 @@ struct fse_handle {
     size_t est_cap = 0;
     bool learned_launch = false;   // the captured graph runs the CNN first
     int learned_n = 0;
+    uint8_t *d_tc_w = nullptr;      // tensor-core network: packed B operands
+    bool tc_net = false;            // 16x16 blocks with a 16-sample border: tcgen05 kernel
+    int *d_err = nullptr;           // device-side error status (bounded waits)
     std::string err = "no error";
 };
 
@@ -315,13 +319,18 @@ __global__ void cnn_gather_kernel(const DevParams P, int first, int count, int M
 }
 
 // network output (estimate / 255) of those blocks -> per-block estimates in
-// sample units, at the caller's block order
+// sample units, at the caller's block order.  The estimate is kept on B and
+// zero on the rest of the area: the iterations then run on the unchanged
+// support and the network supplies what they do not reach (the network is
+// trained for exactly that; see train_init.py).
 __global__ void est_scatter_kernel(const float *__restrict__ out, const BlockRec *__restrict__ blocks, int first,
-                                   int count, int MM, float *__restrict__ est, long long stride) {
+                                   int count, int M, int d, int b, float *__restrict__ est, long long stride) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int MM = M * M;
     if (i >= (long long)count * MM) return;
-    const int q = (int)(i / MM);
-    est[blocks[first + q].orig * stride + i % MM] = 255.f * out[i];
+    const int q = (int)(i / MM), r = (int)(i % MM), am = r / M, an = r % M;
+    const bool inB = am >= d && am < d + b && an >= d && an < d + b;
+    est[blocks[first + q].orig * stride + r] = inB ? 255.f * out[i] : 0.f;
 }
 
 // Model over the whole extrapolation area from the trace of the last launch:
@@ -372,7 +381,14 @@ __global__ void __launch_bounds__(256) area_model_kernel(const DevParams P, floa
 fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     FSE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    if (h->learned_launch) {
+    if (h->learned_launch && h->tc_net) {
+        // learned initialisation on the tensor cores: the network's output on
+        // B straight into h->d_est (zero elsewhere), one persistent launch
+        const unsigned g = (unsigned)std::min(h->learned_n, h->sm_count);
+        fse_tc::cnn_tc_kernel<DevParams, BlockRec><<<g, fse_tc::kThreads, fse_tc::kSmemBytes, h->cap_stream>>>(
+            h->params, h->d_tc_w, h->d_cnn_params, h->d_est, (long long)h->cnn_M * h->cnn_M, h->learned_n,
+            h->d_err);
+    } else if (h->learned_launch) {
         // learned initialisation: CNN over all blocks in chunks, estimates
         // scattered to h->d_est, then the concealment from the residual
         const int M = h->cnn_M, MM = M * M;
@@ -392,7 +408,7 @@ fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) 
             fse_net::conv_fwd_kernel<3><<<cg, 128, 0, h->cap_stream>>>(h->d_cnn_a0, h->d_cnn_wb, h->d_cnn_params,
                                                                        h->d_cnn_out, cnt, M, M);
             est_scatter_kernel<<<(unsigned)((np + 255) / 256), 256, 0, h->cap_stream>>>(
-                h->d_cnn_out, h->d_blocks, first, cnt, MM, h->d_est, (long long)MM);
+                h->d_cnn_out, h->d_blocks, first, cnt, M, C.d, C.b, h->d_est, (long long)MM);
         }
     }
     cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
@@ -579,9 +595,12 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     h->learned_n = n_blocks;
     if (learned) {
         const int MM = h->cnn_M * h->cnn_M;
+        const size_t old_cap = h->est_cap;
         st = grow(h, &h->d_est, &h->est_cap, (size_t)n_blocks * MM);
         if (st != FSE_OK) return st;
-        if (!h->d_cnn_x) {
+        // the tensor-core network writes B only: the rest of every estimate stays 0
+        if (h->est_cap != old_cap) FSE_CUDA(h, cudaMemset(h->d_est, 0, h->est_cap * sizeof(float)));
+        if (!h->tc_net && !h->d_cnn_x) {
             const size_t C = (size_t)h->cnn_chunk;
             FSE_CUDA(h, cudaMalloc(&h->d_cnn_x, C * MM * 2 * sizeof(__nv_bfloat16)));
             FSE_CUDA(h, cudaMalloc(&h->d_cnn_a0, C * MM * 32 * sizeof(__nv_bfloat16)));
@@ -655,6 +674,14 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     if (occ < 1 || occ2 < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
     h->max_ctas_per_sm = occ;
     h->max_ctas_per_sm_256 = occ2;
+    h->tc_net = cfg->init == FSE_INIT_LEARNED && cfg->cls[0].block == 16 && cfg->cls[0].border == 16;
+    if (h->tc_net) {
+        if (prop.major < 10) return bail(fail(h, FSE_ERR_UNSUPPORTED, "learned initialisation needs sm_100 or later"));
+        CREATE_CUDA(cudaFuncSetAttribute(fse_tc::cnn_tc_kernel<DevParams, BlockRec>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, fse_tc::kSmemBytes));
+    }
+    CREATE_CUDA(cudaMalloc(&h->d_err, sizeof(int)));
+    CREATE_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
     CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CREATE_CUDA(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming));
     CREATE_CUDA(cudaMalloc(&h->d_counter, sizeof(int)));
@@ -720,6 +747,12 @@ fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n) {
     const int m = std::max(fse_net::kWbTotal, fse_net::kWtTotal);
     fse_net::pack_weights_kernel<<<(m + 255) / 256, 256>>>(h->d_cnn_params, h->d_cnn_wb, h->d_cnn_wt);
     FSE_CUDA(h, cudaGetLastError());
+    if (h->tc_net) {
+        if (!h->d_tc_w) FSE_CUDA(h, cudaMalloc(&h->d_tc_w, fse_tc::kWBytes));
+        fse_tc::pack_tc_weights_kernel<<<(fse_tc::kWBytes / 2 + 255) / 256, 256>>>(
+            h->d_cnn_params, reinterpret_cast<__nv_bfloat16 *>(h->d_tc_w));
+        FSE_CUDA(h, cudaGetLastError());
+    }
     FSE_CUDA(h, cudaDeviceSynchronize());
     h->weights_loaded = true;
     h->graph_valid = false;   // the captured launch reads the new weights anyway; re-plan to be safe
@@ -800,6 +833,19 @@ fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, 
     return FSE_OK;
 }
 
+fse_status fse_sync(fse_handle *h) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard guard(h->device);
+    FSE_CUDA(h, cudaStreamSynchronize(h->last_stream));
+    int e = 0;
+    FSE_CUDA(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        FSE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        return fail(h, FSE_ERR_TIMEOUT, "a bounded wait of the learned-initialisation kernel expired");
+    }
+    return FSE_OK;
+}
+
 const char *fse_last_error(const fse_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 void fse_destroy(fse_handle *h) {
@@ -823,6 +869,8 @@ void fse_destroy(fse_handle *h) {
         cudaFree(h->d_cnn_wb);
         cudaFree(h->d_cnn_wt);
         cudaFree(h->d_cnn_x);
+        cudaFree(h->d_tc_w);
+        cudaFree(h->d_err);
         cudaFree(h->d_cnn_a0);
         cudaFree(h->d_cnn_a1);
         cudaFree(h->d_cnn_out);

@@ -1,0 +1,402 @@
+// fse_cnn_tc.cuh -- the learned-initialisation network on the lost block, one
+// persistent kernel on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// Only the lost block B's output of the network is used (the estimate is
+// kept on B).  For the 48x48 area of a 16x16 block with a 16-sample border,
+// B = [16, 32)^2 and the receptive field of the four dilated 3x3 layers
+// (radius 1 + 2 + 4 + 8 = 15) stays inside the area, so B's output is that
+// of valid convolutions over shrinking regions, with no zero padding:
+//   layer 3 (d = 8) output B            needs its input on R3 = [8, 40)^2,
+//   layer 2 (d = 4) output R3           needs R2 = [4, 44)^2,
+//   layer 1 (d = 2) output R2           needs R1 = [2, 46)^2,
+//   layer 0 (d = 1) output R1           needs the input on R0 = [1, 47)^2.
+// This is 32.8 M multiply-adds per block instead of 44.5 M for the whole area,
+// with results identical (same operations per output) to the whole-area
+// network on B.
+//
+// One CTA per SM (512 threads), one area at a time:
+//   - the layer input lives in shared memory as four channel-group planes,
+//     plane g = [position][8 channels] (16 bytes per position), positions on
+//     the layer's own region grid (row-major, width W_l).  A layer's outputs
+//     are computed on the same grid (implicit GEMM, M = 128 consecutive grid
+//     positions, N = output channels, K = 9 taps x 32 channels): the A tile of
+//     tap (ky, kx) is the 128 positions shifted by (ky d W + kx d), which in
+//     the plane layout is exactly the no-swizzle K-major canonical layout
+//     (core matrix = 8 positions x 16 bytes, SBO = 128 B between position
+//     groups, LBO = one plane between the two 8-channel halves of a K step);
+//     positions of the grid's margins give unused outputs;
+//   - one thread issues tcgen05.mma (kind::f16, bf16 operands, FP32
+//     accumulators in TMEM, one 32-column accumulator per M tile) and commits
+//     to an mbarrier; 16 warps then drain TMEM (tcgen05.ld), add the bias,
+//     apply ReLU while rounding to bf16 (cvt.rn.relu.bf16x2.f32) and store the
+//     next layer's planes in place (the layer's MMAs have completed);
+//   - layer 0 (2 input channels, K = 18 padded to 32) takes an explicit
+//     im2col in the same plane layout;
+//   - layer 3 (1 output channel) runs with N = 16 (zero weights beyond
+//     channel 0) and its epilogue writes 255 x (acc + bias) on B.
+// Waits on the mbarrier are bounded (1 s of globaltimer); on expiry the
+// kernel records FSE_ERR_TIMEOUT in *err, stops, and frees its TMEM.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "fse_cnn.cuh"
+
+namespace fse_tc {
+
+constexpr int kThreads = 512;
+constexpr int kPlanePos = 2048;                       // positions per channel-group plane
+constexpr int kPlaneBytes = kPlanePos * 16;           // 32 KB
+constexpr int kActBytes = 4 * kPlaneBytes;            // 128 KB
+constexpr int kTileBytes32 = 32 * 16 * 2;             // one K step of a 32-row B operand
+constexpr int kTileBytes16 = 16 * 16 * 2;             // one K step of a 16-row B operand
+constexpr int kW0Off = 0;                              // layer 0: 2 K steps
+constexpr int kW1Off = kW0Off + 2 * kTileBytes32;      // layers 1, 2: 18 K steps (9 taps x 2)
+constexpr int kW2Off = kW1Off + 18 * kTileBytes32;
+constexpr int kW3Off = kW2Off + 18 * kTileBytes32;     // layer 3: 18 K steps, N = 16
+constexpr int kWBytes = kW3Off + 18 * kTileBytes16;    // 47104
+constexpr int kXsPos = 46 * 46;                        // layer-0 input region R0
+constexpr int kOffAct = 0;
+constexpr int kOffW = kOffAct + kActBytes;
+constexpr int kOffXs = kOffW + kWBytes;
+constexpr int kOffBias = kOffXs + ((kXsPos * 4 + 127) / 128) * 128;
+constexpr int kOffBar = kOffBias + 128 * 4;
+constexpr int kSmemBytes = kOffBar + 64;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+constexpr int kTmemCols = 512;
+
+// layer geometry: input grid width W, dilation D, M tiles, next grid width
+__host__ __device__ constexpr int grid_w(int l) { return l == 0 ? 46 : l == 1 ? 44 : l == 2 ? 40 : 32; }
+__host__ __device__ constexpr int tiles_of(int l) { return l == 0 ? 16 : l == 1 ? 14 : l == 2 ? 10 : 4; }
+__host__ __device__ constexpr int ncols_of(int l) { return l == 3 ? 16 : 32; }
+// first output position of the layer's range on its grid: (d, d)
+__host__ __device__ constexpr int first_pos(int l) { return (1 << l) * grid_w(l) + (1 << l); }
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major canonical layout
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: bf16 A and B (K-major), FP32 D
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 8 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// bf16x2 of (relu(lo), relu(hi)), round to nearest even; lo in the low half
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// ------------------------------------------------------------ weights
+// Flat FP32 parameters -> the kernel's shared-memory image of the B operands
+// (bf16, no-swizzle K-major: per K step, core matrices of 8 output channels
+// x 8 K values, [K half][channel group][8][8]).
+static __global__ void pack_tc_weights_kernel(const float *__restrict__ params, __nv_bfloat16 *__restrict__ img) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // bf16 element index
+    if (e >= kWBytes / 2) return;
+    const int byte = 2 * e;
+    int l, base, tb, N;
+    if (byte < kW1Off) { l = 0; base = kW0Off; tb = kTileBytes32; N = 32; }
+    else if (byte < kW2Off) { l = 1; base = kW1Off; tb = kTileBytes32; N = 32; }
+    else if (byte < kW3Off) { l = 2; base = kW2Off; tb = kTileBytes32; N = 32; }
+    else { l = 3; base = kW3Off; tb = kTileBytes16; N = 16; }
+    const int kt = (byte - base) / tb;                 // K step
+    const int w = ((byte - base) % tb) / 2;            // element in the K step
+    const int cm = w / 64, r = (w % 64) / 8, kk = w % 8;
+    const int kh = cm / (N / 8), ng = cm % (N / 8);
+    const int n = ng * 8 + r, kq = kh * 8 + kk;        // output channel, K index in the step
+    const int cin = fse_net::cin_of(l), cout = fse_net::cout_of(l);
+    float v = 0.f;
+    if (l == 0) {
+        const int kg = kt * 16 + kq, tap = kg / 2, ci = kg % 2;
+        if (tap < 9 && n < cout) v = params[fse_net::woff_of(0) + (n * cin + ci) * 9 + tap];
+    } else {
+        const int tap = kt / 2, ci = (kt % 2) * 16 + kq;
+        if (n < cout) v = params[fse_net::woff_of(l) + (n * cin + ci) * 9 + tap];
+    }
+    img[e] = __float2bfloat16_rn(v);
+}
+
+// ------------------------------------------------------------ kernel
+struct Shared {
+    uint8_t *act;
+    const uint8_t *w;
+    uint32_t *xs;
+    float *bias;
+    uint32_t bar;
+    volatile int *flag;
+};
+
+// thread 0 waits for the committed MMAs (bounded), every thread learns the
+// outcome after the barrier
+__device__ __forceinline__ bool wait_mma(const Shared &S, uint32_t parity) {
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = globaltimer();
+        bool done = false;
+        while (!(done = mbar_try_wait(S.bar, parity)))
+            if (globaltimer() - t0 > 1000000000ull) break;
+        *S.flag = done ? 0 : 1;
+    }
+    __syncthreads();
+    const bool ok = *S.flag == 0;
+    fence_after_sync();
+    return ok;
+}
+
+// MMAs of layer L (1..3): tap-major so consecutive MMAs use different
+// accumulators; the first MMA of each tile overwrites it
+template <int L>
+__device__ __forceinline__ void issue_layer(const Shared &S, uint32_t tmem) {
+    constexpr int W = grid_w(L), D = 1 << L, T = tiles_of(L), N = ncols_of(L);
+    constexpr int WOFF = L == 1 ? kW1Off : L == 2 ? kW2Off : kW3Off;
+    constexpr int TB = N == 32 ? kTileBytes32 : kTileBytes16;
+    constexpr uint32_t idesc = make_idesc(128, N);
+    const uint32_t a0 = smem_addr(S.act), b0 = smem_addr(S.w) + WOFF;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int shift = (tap / 3) * D * W + (tap % 3) * D;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t bdesc = make_desc(b0 + (tap * 2 + ks) * TB, (N / 8) * 128, 128);
+#pragma unroll 1
+            for (int t = 0; t < T; ++t) {
+                const uint64_t adesc = make_desc(a0 + 2 * ks * kPlaneBytes + (t * 128 + shift) * 16, kPlaneBytes, 128);
+                mma_bf16(tmem + t * N, adesc, bdesc, idesc, (tap | ks) != 0);
+            }
+        }
+    }
+    mma_commit(S.bar);
+}
+
+// drain layer L's accumulators: bias, ReLU, bf16 -> next layer's planes
+template <int L>
+__device__ __forceinline__ void epilogue_hidden(const Shared &S, uint32_t tmem) {
+    constexpr int W = grid_w(L), D = 1 << L, T = tiles_of(L), WN = grid_w(L + 1);
+    constexpr int P0 = L == 0 ? 47 : first_pos(L);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, cg = warp >> 2;   // TMEM lanes 32*quarter.., channels 8*cg..
+    const float *bias = S.bias + 32 * L + 8 * cg;
+#pragma unroll 1
+    for (int t = 0; t < T; ++t) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + t * 32 + cg * 8, v);
+        const int p = P0 + t * 128 + quarter * 32 + lane;
+        const int y = p / W, x = p % W;
+        if (y >= D && y < W - D && x >= D && x < W - D) {
+            const int q = (y - D) * WN + (x - D);
+            uint4 o;
+            o.x = relu_bf16x2(v[0] + bias[0], v[1] + bias[1]);
+            o.y = relu_bf16x2(v[2] + bias[2], v[3] + bias[3]);
+            o.z = relu_bf16x2(v[4] + bias[4], v[5] + bias[5]);
+            o.w = relu_bf16x2(v[6] + bias[6], v[7] + bias[7]);
+            *reinterpret_cast<uint4 *>(S.act + cg * kPlaneBytes + q * 16) = o;
+        }
+    }
+}
+
+template <class Params, class Rec>
+__global__ void __launch_bounds__(kThreads, 1)
+    cnn_tc_kernel(const Params P, const uint8_t *__restrict__ wimg, const float *__restrict__ params,
+                  float *__restrict__ est, long long est_stride, int n_blocks, int *__restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    Shared S;
+    S.act = smem + kOffAct;
+    S.w = smem + kOffW;
+    S.xs = reinterpret_cast<uint32_t *>(smem + kOffXs);
+    S.bias = reinterpret_cast<float *>(smem + kOffBias);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kOffBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffBar + 8);
+    S.flag = reinterpret_cast<volatile int *>(smem + kOffBar + 12);
+    S.bar = smem_addr(bar);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int i = tid; i < kWBytes / 16; i += kThreads)
+        reinterpret_cast<uint4 *>(smem + kOffW)[i] = reinterpret_cast<const uint4 *>(wimg)[i];
+    if (tid < 97) {
+        const int l = tid / 32, c = tid % 32;
+        S.bias[tid] = params[fse_net::woff_of(l) + fse_net::cout_of(l) * fse_net::cin_of(l) * 9 + c];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    uint32_t parity = 0;
+    bool ok = true;
+
+    for (int qb = blockIdx.x; qb < n_blocks && ok; qb += gridDim.x) {
+        const Rec blk = P.blocks[qb];
+        // ---- layer-0 input on R0 = [1, 47)^2 of the area (as cnn_gather) ----
+        for (int g = tid; g < kXsPos; g += kThreads) {
+            const int am = g / 46 + 1, an = g % 46 + 1;
+            const int yy = blk.y - 16 + am, xx = blk.x - 16 + an;
+            const bool inB = am >= 16 && am < 32 && an >= 16 && an < 32;
+            float sv = 0.f, a = 0.f;
+            if (!inB && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W &&
+                P.mask[((size_t)blk.image * P.H + yy) * P.W + xx] == 0) {
+                const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+                sv = (P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
+                                   : reinterpret_cast<const float *>(row)[xx]) *
+                     (1.f / 255.f);
+                a = 1.f;
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(sv, a);
+            S.xs[g] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        __syncthreads();
+        // ---- layer-0 im2col: position i <-> grid position 47 + i, K = 2 tap + channel ----
+        for (int i = tid; i < kPlanePos; i += kThreads) {
+            const int p = 47 + i, y = p / 46, x = p % 46;
+            const bool valid = y >= 1 && y <= 44 && x >= 1 && x <= 44;
+            uint32_t v[16];
+#pragma unroll
+            for (int tap = 0; tap < 16; ++tap)
+                v[tap] = (tap < 9 && valid) ? S.xs[(y + tap / 3 - 1) * 46 + x + tap % 3 - 1] : 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                *reinterpret_cast<uint4 *>(S.act + j * kPlaneBytes + i * 16) =
+                    make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        fence_proxy_async();
+        fence_before_sync();
+        __syncthreads();
+        // ---- layer 0 ----
+        if (tid == 0) {
+            fence_after_sync();
+            const uint32_t a0 = smem_addr(S.act), b0 = smem_addr(S.w) + kW0Off;
+            constexpr uint32_t idesc = make_idesc(128, 32);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t bdesc = make_desc(b0 + ks * kTileBytes32, 4 * 128, 128);
+#pragma unroll 1
+                for (int t = 0; t < 16; ++t)
+                    mma_bf16(tmem + t * 32, make_desc(a0 + 2 * ks * kPlaneBytes + t * 128 * 16, kPlaneBytes, 128),
+                             bdesc, idesc, ks);
+            }
+            mma_commit(S.bar);
+        }
+        if (!(ok = wait_mma(S, parity))) break;
+        parity ^= 1u;
+        epilogue_hidden<0>(S, tmem);
+        fence_proxy_async();
+        fence_before_sync();
+        __syncthreads();
+        // ---- layers 1, 2 ----
+        if (tid == 0) { fence_after_sync(); issue_layer<1>(S, tmem); }
+        if (!(ok = wait_mma(S, parity))) break;
+        parity ^= 1u;
+        epilogue_hidden<1>(S, tmem);
+        fence_proxy_async();
+        fence_before_sync();
+        __syncthreads();
+        if (tid == 0) { fence_after_sync(); issue_layer<2>(S, tmem); }
+        if (!(ok = wait_mma(S, parity))) break;
+        parity ^= 1u;
+        epilogue_hidden<2>(S, tmem);
+        fence_proxy_async();
+        fence_before_sync();
+        __syncthreads();
+        // ---- layer 3: channel 0 on B ----
+        if (tid == 0) { fence_after_sync(); issue_layer<3>(S, tmem); }
+        if (!(ok = wait_mma(S, parity))) break;
+        parity ^= 1u;
+        if (warp < 4) {
+            const float b3 = S.bias[96];
+#pragma unroll 1
+            for (int t = 0; t < tiles_of(3); ++t) {
+                const float v = tmem_ld1(tmem + ((uint32_t)(warp * 32) << 16) + t * 16);
+                const int p = first_pos(3) + t * 128 + warp * 32 + lane;
+                const int y = p / 32, x = p % 32;
+                if (y >= 8 && y < 24 && x >= 8 && x < 24)
+                    est[(long long)blk.orig * est_stride + (y + 8) * 48 + (x + 8)] = 255.f * (v + b3);
+            }
+        }
+        fence_before_sync();
+        __syncthreads();   // TMEM and the planes are reused by the next area
+    }
+    if (!ok && tid == 0) atomicExch(err, 5);
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace fse_tc

@@ -15,13 +15,18 @@ whole area (target "model"; the residual s - e the iterations then see is
 what the plain model left unexplained plus the network's own error, which
 they go on to model); with target "support", the support samples
 themselves on the support and the plain extrapolation on the lost block;
-with target "correction", zero on the support and, on the lost block, what
-the plain extrapolation at I = 200 adds to the one at I = short_iters (the
-iterations then run on the unchanged support, and the network supplies the
-detail the short run misses).
-Loss weights: the weighting function of Eq. (3) on the support (the weight
-the model fitting gives the residual there), lam_b on the lost block, 0
-elsewhere (outside the frame, other lost samples).
+with target "correction" (the default, and the reading the library's
+learned launch uses), only the lost block counts: there the target is what
+the plain extrapolation at I = 200 adds to the one at I = short_iters.  In
+use the estimate is kept on the lost block only, the iterations run on the
+unchanged support, and the network supplies the detail the short run
+misses.  Measured on held-out frames (20k areas): the "model" reading left
+the network's error on the lost block uncorrected (20.4 dB at I = 50 against
+30.1 dB plain), the "correction" reading gains over plain at I = 50.
+Loss weights: lam_b on the lost block; for "model" and "support" also the
+weighting function of Eq. (3) on the support (the weight the model fitting
+gives the residual there); 0 elsewhere (outside the frame, other lost
+samples).
 Test frames come from disjoint seeds.  PSNR is taken over all lost samples
 against the original frame, with outputs clipped to [0, 255].
 
@@ -174,7 +179,10 @@ def training_set(frames, mask, blocks, lam_b: float, target: str = "model", shor
         t = s / 255.0
         t[:, D:D + B, D:D + B] = fse / 255.0
     w = weight_table(frames.device)
-    lam = torch.where(sup, w[None].expand_as(s), torch.zeros((), device=s.device))
+    if target == "correction":      # only the lost block's output is used
+        lam = torch.zeros_like(s)
+    else:
+        lam = torch.where(sup, w[None].expand_as(s), torch.zeros((), device=s.device))
     lam[:, D:D + B, D:D + B] = lam_b
     return x, t.contiguous(), lam.contiguous()
 
@@ -205,9 +213,9 @@ def train(x, t, lam, steps: int, batch: int, lr: float, seed: int, init=None, lo
     return p, hist
 
 
-def evaluate(frames, mask, blocks, params, iters=(0, 50, 200)):
-    """PSNR on the lost samples: plain extrapolation at each I, learned
-    initialisation followed by each I."""
+def evaluate(frames, mask, blocks, params, plain_iters=(50, 60, 70, 80, 100, 150, 200), learned_iters=(0, 50)):
+    """PSNR on the lost samples: plain extrapolation at each I of
+    plain_iters, learned initialisation followed by each I of learned_iters."""
     import torch
     from . import Engine
     truth = truth_patches(frames, blocks)
@@ -221,9 +229,9 @@ def evaluate(frames, mask, blocks, params, iters=(0, 50, 200)):
     eng.close()
     out["warm_from_plain_i200_model_i50_psnr"] = psnr(p.view(len(blocks), B, B), truth)
     del g200
-    for I in iters:
-        if I > 0:
-            out[f"plain_i{I}_psnr"] = psnr(plain_patches(frames, mask, blocks, I), truth)
+    for I in plain_iters:
+        out[f"plain_i{I}_psnr"] = psnr(plain_patches(frames, mask, blocks, I), truth)
+    for I in learned_iters:
         out[f"learned_i{I}_psnr"] = psnr(learned_patches(frames, mask, blocks, params, I), truth)
     return out
 
@@ -241,7 +249,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lam-b", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=7)
-    ap.add_argument("--target", choices=["model", "support", "correction"], default="model")
+    ap.add_argument("--target", choices=["model", "support", "correction"], default="correction")
     ap.add_argument("--short-iters", type=int, default=50)
     ap.add_argument("--init", default=None, help="start from these parameters (.f32)")
     a = ap.parse_args(argv)

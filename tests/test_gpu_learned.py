@@ -86,19 +86,27 @@ def _learned(P, img, mask, blocks, cls, weights, init_iters, trace=False):
     dmask = torch.from_numpy(mask).cuda()
     patches = torch.zeros(eng.patch_total(blocks), dtype=torch.float32, device="cuda")
     eng.run(dimg, dmask, blocks, patches=patches)
+    eng.sync()                       # raises on an expired device-side wait
     torch.cuda.synchronize()
     tr = eng.trace() if trace else None
     eng.close()
     return patches.cpu().numpy(), tr
 
 
-def test_learned_estimate_matches_network_oracle(P):
-    """Zero FSE iterations: the output on each block is the network's estimate."""
+@pytest.mark.parametrize("geom", ["b16d16", "b8d12"])
+def test_learned_estimate_matches_network_oracle(P, geom):
+    """Zero FSE iterations: the output on each block is the network's estimate
+    (16x16 blocks with a 16-sample border: the tensor-core kernel on B;
+    other geometries: the whole-area network in chunks)."""
     img, mask, blocks = _learned_scene()
     w = P.he_init(43)
-    cls = dict(C64, iters=0)
+    if geom == "b16d16":
+        cls, b, d = dict(C64, iters=0), 16, 16
+    else:
+        cls, b, d = dict(C32, iters=0), 8, 12
+        blocks = synth.grid_losses(46, 256, 256, 8, 0.2, non_adjacent=True)
+        mask = synth.loss_mask(blocks, [8], 1, 256, 256)
     patches, _ = _learned(P, img, mask, blocks, cls, w, 0)
-    b, d = 16, 16
     x = np.stack([oimage.cnn_input(img[0], mask[0], int(bx), int(by), b, d) for _, bx, by, _c in blocks])
     ref = 255.0 * ocnn.forward(w.astype(np.float64), x.astype(np.float32).astype(np.float64))
     ref_b = ref[:, d:d + b, d:d + b].reshape(len(blocks), -1)
@@ -111,9 +119,9 @@ def test_learned_estimate_matches_network_oracle(P):
 
 
 def test_learned_pipeline_equals_warm_start_from_network(P):
-    """The captured learned pipeline (network, then init_iters FSE iterations
-    on the residual) gives what the warm start gives on the standalone
-    network forward of the same input."""
+    """The captured learned pipeline (network, its output kept on B as the
+    estimate, then init_iters FSE iterations) gives what the warm start gives
+    on the standalone network forward of the same input, cropped to B."""
     img, mask, blocks = _learned_scene()
     w = P.he_init(44)
     b, d, M = 16, 16, 48
@@ -128,16 +136,22 @@ def test_learned_pipeline_equals_warm_start_from_network(P):
     net = P.Cnn(M, M, max_batch=len(blocks))
     net.set_params(w)
     y = net.forward(torch.from_numpy(np.ascontiguousarray(x)).cuda())
-    est = (y * 255.0).reshape(len(blocks), M * M).contiguous()
+    est = torch.zeros_like(y)
+    est[:, d:d + b, d:d + b] = y[:, d:d + b, d:d + b] * 255.0
+    est = est.reshape(len(blocks), M * M).contiguous()
     net.close()
     eng = P.Engine([dict(C64, iters=60)])
     patches = torch.zeros(len(blocks) * b * b, dtype=torch.float32, device="cuda")
     eng.run_init(torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda(), blocks, est, patches=patches)
     torch.cuda.synchronize()
     eng.close()
+    # the two network implementations (tensor-core kernel on B, chunked
+    # whole-area kernels) accumulate in different orders: CNN tolerances
     diff = np.abs(patches.cpu().numpy() - learned)
-    print("learned vs warm start: max", diff.max())
-    assert diff.max() <= 1e-3
+    rms = float(torch.sqrt((est ** 2).sum() / (len(blocks) * b * b)))
+    print("learned vs warm start: max", diff.max(), "p99.9", np.quantile(diff, 0.999), "rms", rms)
+    assert diff.max() <= 2.0 ** -6 * rms
+    assert np.quantile(diff, 0.999) <= 2.0 ** -9 * rms
 
 
 def test_learned_trace_stride_follows_init_iters(P):
