@@ -25,9 +25,10 @@
 //     (core matrix = 8 positions x 16 bytes, SBO = 128 B between position
 //     groups, LBO = one plane between the two 8-channel halves of a K step);
 //     positions of the grid's margins give unused outputs;
-//   - one thread issues tcgen05.mma (kind::f16, bf16 operands, FP32
-//     accumulators in TMEM, one 32-column accumulator per M tile) and commits
-//     to an mbarrier; 16 warps then drain TMEM (tcgen05.ld), add the bias,
+//   - warps 0-3 issue tcgen05.mma (one elected lane each, M tile t by warp
+//     t % 4; kind::f16, bf16 operands, FP32 accumulators in TMEM, one
+//     32-column accumulator per M tile) and each commits to an mbarrier that
+//     completes on the four arrivals; 16 warps then drain TMEM (tcgen05.ld), add the bias,
 //     apply ReLU while rounding to bf16 (cvt.rn.relu.bf16x2.f32) and store the
 //     next layer's planes in place (the layer's MMAs have completed);
 //   - layer 0 (2 input channels, K = 18 padded to 32) takes an explicit
@@ -62,10 +63,16 @@ constexpr int kOffAct = 0;
 constexpr int kOffW = kOffAct + kActBytes;
 constexpr int kOffXs = kOffW + kWBytes;
 constexpr int kOffBias = kOffXs + ((kXsPos * 4 + 127) / 128) * 128;
-constexpr int kOffBar = kOffBias + 128 * 4;
+// epilogue position tables (int16, one per M-tile row): the next layer's
+// plane position of each output, -1 on the grid's margins (layer 3: the
+// estimate's offset in the area)
+constexpr int kTabRows = (16 + 14 + 10 + 4) * 128;
+constexpr int kOffTab = kOffBias + 128 * 4;
+constexpr int kOffBar = kOffTab + kTabRows * 2;
 constexpr int kSmemBytes = kOffBar + 64;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 constexpr int kTmemCols = 512;
+constexpr int kIssuers = 4;   // warps issuing MMAs (one per SM sub-partition); tile t belongs to warp t % 4
 
 // layer geometry: input grid width W, dilation D, M tiles, next grid width
 __host__ __device__ constexpr int grid_w(int l) { return l == 0 ? 46 : l == 1 ? 44 : l == 2 ? 40 : 32; }
@@ -73,6 +80,7 @@ __host__ __device__ constexpr int tiles_of(int l) { return l == 0 ? 16 : l == 1 
 __host__ __device__ constexpr int ncols_of(int l) { return l == 3 ? 16 : 32; }
 // first output position of the layer's range on its grid: (d, d)
 __host__ __device__ constexpr int first_pos(int l) { return (1 << l) * grid_w(l) + (1 << l); }
+__host__ __device__ constexpr int tab_off(int l) { return l == 0 ? 0 : tab_off(l - 1) + tiles_of(l - 1) * 128; }
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -90,18 +98,26 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Executed by a whole warp with warp-uniform operands (so they stay in
+// uniform registers); elect.sync picks one lane (always the same: the lowest)
+// to issue the MMA.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .pred p, e;\n\t.reg .b32 l;\n\t"
+        "elect.sync l|e, 0xffffffff;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// commit, by the lane that issued the MMAs (whole warp executes this)
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t.reg .b32 l;\n\t"
+        "elect.sync l|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_before_sync() {
@@ -128,22 +144,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// 8 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-    uint32_t r[8];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
+// one FP32 accumulator column of this warp's 32 TMEM lanes (the wait names
+// the register, so no use of it can be scheduled before the load completes)
 __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     uint32_t r;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r)::"memory");
     return __uint_as_float(r);
 }
 
@@ -190,6 +196,7 @@ struct Shared {
     const uint8_t *w;
     uint32_t *xs;
     float *bias;
+    int16_t *tab;
     uint32_t bar;
     volatile int *flag;
 };
@@ -212,51 +219,98 @@ __device__ __forceinline__ bool wait_mma(const Shared &S, uint32_t parity) {
 
 // MMAs of layer L (1..3): tap-major so consecutive MMAs use different
 // accumulators; the first MMA of each tile overwrites it
+// The issuing thread runs alone while the other warps wait, so every MMA's
+// operands come from one base descriptor plus compile-time offsets (the
+// start address is the descriptor's low field; offsets stay below its
+// 14-bit range) and the tile loop is unrolled: the issue cost per MMA is a
+// few independent instructions, not a dependent address computation.
 template <int L>
-__device__ __forceinline__ void issue_layer(const Shared &S, uint32_t tmem) {
+__device__ __forceinline__ void issue_layer(const Shared &S, uint32_t tmem, int w) {
     constexpr int W = grid_w(L), D = 1 << L, T = tiles_of(L), N = ncols_of(L);
     constexpr int WOFF = L == 1 ? kW1Off : L == 2 ? kW2Off : kW3Off;
     constexpr int TB = N == 32 ? kTileBytes32 : kTileBytes16;
     constexpr uint32_t idesc = make_idesc(128, N);
-    const uint32_t a0 = smem_addr(S.act), b0 = smem_addr(S.w) + WOFF;
-#pragma unroll 1
+    const uint64_t abase = make_desc(smem_addr(S.act), kPlaneBytes, 128);
+    const uint64_t bbase = make_desc(smem_addr(S.w) + WOFF, (N / 8) * 128, 128);
+#pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
         const int shift = (tap / 3) * D * W + (tap % 3) * D;
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t bdesc = make_desc(b0 + (tap * 2 + ks) * TB, (N / 8) * 128, 128);
-#pragma unroll 1
-            for (int t = 0; t < T; ++t) {
-                const uint64_t adesc = make_desc(a0 + 2 * ks * kPlaneBytes + (t * 128 + shift) * 16, kPlaneBytes, 128);
-                mma_bf16(tmem + t * N, adesc, bdesc, idesc, (tap | ks) != 0);
+            const uint64_t bdesc = bbase + (uint64_t)(((tap * 2 + ks) * TB) >> 4);
+            const uint64_t atk = abase + (uint64_t)((2 * ks * kPlaneBytes + shift * 16) >> 4);
+#pragma unroll
+            for (int j = 0; j < (T + kIssuers - 1) / kIssuers; ++j) {
+                const int t = w + kIssuers * j;
+                if (t < T) mma_bf16(tmem + t * N, atk + (uint64_t)(t * 128), bdesc, idesc, (tap | ks) != 0);
             }
         }
     }
     mma_commit(S.bar);
 }
 
+// the layer-0 input on R0 = [1, 47)^2 of the area (support samples / 255 and
+// the support indicator, as bf16 pairs), by threads first .. kThreads-1
+template <class Params, class Rec>
+__device__ __forceinline__ void stage_input(const Params &P, const Rec &blk, uint32_t *xs, int first) {
+    if ((int)threadIdx.x < first) return;
+    for (int g = threadIdx.x - first; g < kXsPos; g += kThreads - first) {
+        const int am = g / 46 + 1, an = g % 46 + 1;
+        const int yy = blk.y - 16 + am, xx = blk.x - 16 + an;
+        const bool inB = am >= 16 && am < 32 && an >= 16 && an < 32;
+        float sv = 0.f, a = 0.f;
+        if (!inB && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W &&
+            P.mask[((size_t)blk.image * P.H + yy) * P.W + xx] == 0) {
+            const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+            sv = (P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
+                               : reinterpret_cast<const float *>(row)[xx]) *
+                 (1.f / 255.f);
+            a = 1.f;
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(sv, a);
+        xs[g] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+}
+
 // drain layer L's accumulators: bias, ReLU, bf16 -> next layer's planes
 template <int L>
 __device__ __forceinline__ void epilogue_hidden(const Shared &S, uint32_t tmem) {
-    constexpr int W = grid_w(L), D = 1 << L, T = tiles_of(L), WN = grid_w(L + 1);
-    constexpr int P0 = L == 0 ? 47 : first_pos(L);
+    constexpr int T = tiles_of(L);
+    static_assert(T % 2 == 0, "tiles are drained in pairs");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter = warp & 3, cg = warp >> 2;   // TMEM lanes 32*quarter.., channels 8*cg..
-    const float *bias = S.bias + 32 * L + 8 * cg;
+    float b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) b[j] = S.bias[32 * L + 8 * cg + j];
+    const int16_t *tab = S.tab + tab_off(L) + quarter * 32 + lane;
+    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + cg * 8;
+    uint8_t *dst = S.act + cg * kPlaneBytes;
 #pragma unroll 1
-    for (int t = 0; t < T; ++t) {
-        float v[8];
-        tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + t * 32 + cg * 8, v);
-        const int p = P0 + t * 128 + quarter * 32 + lane;
-        const int y = p / W, x = p % W;
-        if (y >= D && y < W - D && x >= D && x < W - D) {
-            const int q = (y - D) * WN + (x - D);
-            uint4 o;
-            o.x = relu_bf16x2(v[0] + bias[0], v[1] + bias[1]);
-            o.y = relu_bf16x2(v[2] + bias[2], v[3] + bias[3]);
-            o.z = relu_bf16x2(v[4] + bias[4], v[5] + bias[5]);
-            o.w = relu_bf16x2(v[6] + bias[6], v[7] + bias[7]);
-            *reinterpret_cast<uint4 *>(S.act + cg * kPlaneBytes + q * 16) = o;
+    for (int t = 0; t < T; t += 2) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tbase + t * 32), "r"(tbase + (t + 1) * 32));
+        const int q0 = tab[t * 128], q1 = tab[(t + 1) * 128];
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                       "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                       "+r"(r[14]), "+r"(r[15])::"memory");
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = h ? q1 : q0;
+            const uint32_t *v = r + 8 * h;
+            if (q >= 0) {
+                uint4 o;
+                o.x = relu_bf16x2(__uint_as_float(v[0]) + b[0], __uint_as_float(v[1]) + b[1]);
+                o.y = relu_bf16x2(__uint_as_float(v[2]) + b[2], __uint_as_float(v[3]) + b[3]);
+                o.z = relu_bf16x2(__uint_as_float(v[4]) + b[4], __uint_as_float(v[5]) + b[5]);
+                o.w = relu_bf16x2(__uint_as_float(v[6]) + b[6], __uint_as_float(v[7]) + b[7]);
+                *reinterpret_cast<uint4 *>(dst + q * 16) = o;
+            }
         }
     }
 }
@@ -271,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     S.w = smem + kOffW;
     S.xs = reinterpret_cast<uint32_t *>(smem + kOffXs);
     S.bias = reinterpret_cast<float *>(smem + kOffBias);
+    S.tab = reinterpret_cast<int16_t *>(smem + kOffTab);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kOffBar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffBar + 8);
     S.flag = reinterpret_cast<volatile int *>(smem + kOffBar + 12);
@@ -283,8 +338,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int l = tid / 32, c = tid % 32;
         S.bias[tid] = params[fse_net::woff_of(l) + fse_net::cout_of(l) * fse_net::cin_of(l) * 9 + c];
     }
+    // position tables of the four epilogues (same for every area)
+    for (int i = tid; i < kTabRows; i += kThreads) {
+        int l = 0;
+        while (l < 3 && i >= tab_off(l + 1)) ++l;
+        const int r = i - tab_off(l);
+        const int W = grid_w(l), D = 1 << l;
+        const int p = (l == 0 ? 47 : first_pos(l)) + r, y = p / W, x = p % W;
+        int q = -1;
+        if (y >= D && y < W - D && x >= D && x < W - D)
+            q = l < 3 ? (y - D) * grid_w(l + 1) + (x - D) : (y + 8) * 48 + (x + 8);
+        S.tab[i] = (int16_t)q;
+    }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(S.bar), "r"(kIssuers) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -300,26 +367,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t parity = 0;
     bool ok = true;
 
+    if (blockIdx.x < n_blocks) stage_input(P, P.blocks[blockIdx.x], S.xs, 0);
+    __syncthreads();
     for (int qb = blockIdx.x; qb < n_blocks && ok; qb += gridDim.x) {
         const Rec blk = P.blocks[qb];
-        // ---- layer-0 input on R0 = [1, 47)^2 of the area (as cnn_gather) ----
-        for (int g = tid; g < kXsPos; g += kThreads) {
-            const int am = g / 46 + 1, an = g % 46 + 1;
-            const int yy = blk.y - 16 + am, xx = blk.x - 16 + an;
-            const bool inB = am >= 16 && am < 32 && an >= 16 && an < 32;
-            float sv = 0.f, a = 0.f;
-            if (!inB && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W &&
-                P.mask[((size_t)blk.image * P.H + yy) * P.W + xx] == 0) {
-                const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
-                sv = (P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
-                                   : reinterpret_cast<const float *>(row)[xx]) *
-                     (1.f / 255.f);
-                a = 1.f;
-            }
-            const __nv_bfloat162 h = __floats2bfloat162_rn(sv, a);
-            S.xs[g] = *reinterpret_cast<const uint32_t *>(&h);
-        }
-        __syncthreads();
         // ---- layer-0 im2col: position i <-> grid position 47 + i, K = 2 tap + channel ----
         for (int i = tid; i < kPlanePos; i += kThreads) {
             const int p = 47 + i, y = p / 46, x = p % 46;
@@ -337,17 +388,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before_sync();
         __syncthreads();
         // ---- layer 0 ----
-        if (tid == 0) {
+        if (warp < kIssuers) {
             fence_after_sync();
-            const uint32_t a0 = smem_addr(S.act), b0 = smem_addr(S.w) + kW0Off;
             constexpr uint32_t idesc = make_idesc(128, 32);
+            const uint64_t abase = make_desc(smem_addr(S.act), kPlaneBytes, 128);
+            const uint64_t bbase = make_desc(smem_addr(S.w) + kW0Off, 4 * 128, 128);
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t bdesc = make_desc(b0 + ks * kTileBytes32, 4 * 128, 128);
-#pragma unroll 1
-                for (int t = 0; t < 16; ++t)
-                    mma_bf16(tmem + t * 32, make_desc(a0 + 2 * ks * kPlaneBytes + t * 128 * 16, kPlaneBytes, 128),
-                             bdesc, idesc, ks);
+                const uint64_t bdesc = bbase + (uint64_t)((ks * kTileBytes32) >> 4);
+                const uint64_t ak = abase + (uint64_t)((2 * ks * kPlaneBytes) >> 4);
+#pragma unroll
+                for (int j = 0; j < 16 / kIssuers; ++j) {
+                    const int t = warp + kIssuers * j;
+                    mma_bf16(tmem + t * 32, ak + (uint64_t)(t * 128), bdesc, idesc, ks);
+                }
             }
             mma_commit(S.bar);
         }
@@ -358,14 +412,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before_sync();
         __syncthreads();
         // ---- layers 1, 2 ----
-        if (tid == 0) { fence_after_sync(); issue_layer<1>(S, tmem); }
+        if (warp < kIssuers) { fence_after_sync(); issue_layer<1>(S, tmem, warp); }
+        // while layer 1 runs: the next area's input (xs is free since the im2col)
+        if (warp >= kIssuers && qb + (int)gridDim.x < n_blocks)
+            stage_input(P, P.blocks[qb + gridDim.x], S.xs, 32 * kIssuers);
         if (!(ok = wait_mma(S, parity))) break;
         parity ^= 1u;
         epilogue_hidden<1>(S, tmem);
         fence_proxy_async();
         fence_before_sync();
         __syncthreads();
-        if (tid == 0) { fence_after_sync(); issue_layer<2>(S, tmem); }
+        if (warp < kIssuers) { fence_after_sync(); issue_layer<2>(S, tmem, warp); }
         if (!(ok = wait_mma(S, parity))) break;
         parity ^= 1u;
         epilogue_hidden<2>(S, tmem);
@@ -373,18 +430,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before_sync();
         __syncthreads();
         // ---- layer 3: channel 0 on B ----
-        if (tid == 0) { fence_after_sync(); issue_layer<3>(S, tmem); }
+        if (warp < kIssuers) { fence_after_sync(); issue_layer<3>(S, tmem, warp); }
         if (!(ok = wait_mma(S, parity))) break;
         parity ^= 1u;
         if (warp < 4) {
             const float b3 = S.bias[96];
-#pragma unroll 1
+#pragma unroll
             for (int t = 0; t < tiles_of(3); ++t) {
                 const float v = tmem_ld1(tmem + ((uint32_t)(warp * 32) << 16) + t * 16);
-                const int p = first_pos(3) + t * 128 + warp * 32 + lane;
-                const int y = p / 32, x = p % 32;
-                if (y >= 8 && y < 24 && x >= 8 && x < 24)
-                    est[(long long)blk.orig * est_stride + (y + 8) * 48 + (x + 8)] = 255.f * (v + b3);
+                const int q = S.tab[tab_off(3) + t * 128 + warp * 32 + lane];
+                if (q >= 0) est[(long long)blk.orig * est_stride + q] = 255.f * (v + b3);
             }
         }
         fence_before_sync();
