@@ -39,6 +39,9 @@ LOSS = 0.10
 METRIC = "16x16 blocks/s at I=200, 64x64 FFT"
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "fse_batch_kernel_4k64_i200.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2204_14193_gb300", "csrc", "fse_device.cuh")
+# multiply-adds of the network outputs that reach a 16x16 block (layers 0..3:
+# 44^2 x 32 x 18, 40^2 x 32 x 288, 32^2 x 32 x 288, 16^2 x 1 x 288), x2 flops
+NET_FLOPS_PER_BLOCK = 2.0 * (44 * 44 * 32 * 18 + 40 * 40 * 32 * 288 + 32 * 32 * 32 * 288 + 16 * 16 * 288)
 
 
 def parse():
@@ -235,11 +238,27 @@ def learned_leg(P, vid, mask, blocks, plain_patches, args, stream, dev):
     eng = P.Engine([dict(CLS, iters=args.init_iters)])
     ms_p = timed_runs(eng, vid, mask, blocks, pl, k, max(args.warmup, 2), stream, dev)
     eng.close()
+    net_ms = ms - ms_p
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained")
+    achieved = n * NET_FLOPS_PER_BLOCK / (net_ms / 1e3) / 1e12 if net_ms > 0 else None
     out.update({f"plain_i{args.init_iters}_blocks_per_s": n / (ms_p / 1e3),
                 f"plain_i{args.init_iters}_psnr_db": ps(pl),
-                "network_ms_per_step_est": ms - ms_p,
+                "network_ms_per_step_est": net_ms,
+                "network_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak if (achieved and peak) else None,
+                                     "basis": "network time = learned step - plain step at the same I; "
+                                              f"{NET_FLOPS_PER_BLOCK / 1e6:.2f} MFLOP per block (the valid "
+                                              "convolutions that reach B); peak = measured sustained bf16"},
                 "weights": os.path.relpath(train_init.weights_path(), ROOT)})
     return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
 def iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, peak_gbs):
