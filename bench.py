@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the I sweep and the uneven-size batch")
     ap.add_argument("--init-iters", type=int, default=50)
+    ap.add_argument("--init-weights", default=None, help="network parameters (.f32) for the learned leg")
     return ap.parse_args()
 
 
@@ -222,7 +223,7 @@ def learned_leg(P, vid, mask, blocks, plain_patches, args, stream, dev):
     import torch
     from paper_2204_14193_gb300 import train_init
     try:
-        w = train_init.load_weights()
+        w = train_init.load_weights(args.init_weights)
     except (OSError, ValueError) as e:
         return {"available": False, "why": str(e)}
     n = len(blocks)
@@ -250,7 +251,7 @@ def learned_leg(P, vid, mask, blocks, plain_patches, args, stream, dev):
                                      "basis": "network time = learned step - plain step at the same I; "
                                               f"{NET_FLOPS_PER_BLOCK / 1e6:.2f} MFLOP per block (the valid "
                                               "convolutions that reach B); peak = measured sustained bf16"},
-                "weights": os.path.relpath(train_init.weights_path(), ROOT)})
+                "weights": os.path.relpath(args.init_weights or train_init.weights_path(), ROOT)})
     return out
 
 

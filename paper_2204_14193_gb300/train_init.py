@@ -252,8 +252,13 @@ def main(argv=None):
     ap.add_argument("--target", choices=["model", "support", "correction"], default="correction")
     ap.add_argument("--short-iters", type=int, default=50)
     ap.add_argument("--init", default=None, help="start from these parameters (.f32)")
+    ap.add_argument("--eval-only", default=None, help="evaluate these parameters (.f32) and exit")
     a = ap.parse_args(argv)
     import torch
+    if a.eval_only:
+        fr, mk, bl = frames_and_losses(TEST_SEED0, a.test_frames, a.height, a.width, a.loss)
+        print(json.dumps(evaluate(fr, mk, bl, load_weights(a.eval_only))), flush=True)
+        return
     os.makedirs(a.out, exist_ok=True)
     t0 = time.time()
     fr, mk, bl = frames_and_losses(TRAIN_SEED0, a.train_frames, a.height, a.width, a.loss)

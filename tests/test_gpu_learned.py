@@ -93,14 +93,16 @@ def _learned(P, img, mask, blocks, cls, weights, init_iters, trace=False):
     return patches.cpu().numpy(), tr
 
 
-@pytest.mark.parametrize("geom", ["b16d16", "b8d12"])
+@pytest.mark.parametrize("geom", ["b16d16", "b8d12", "b16d16_f32"])
 def test_learned_estimate_matches_network_oracle(P, geom):
     """Zero FSE iterations: the output on each block is the network's estimate
     (16x16 blocks with a 16-sample border: the tensor-core kernel on B;
     other geometries: the whole-area network in chunks)."""
     img, mask, blocks = _learned_scene()
     w = P.he_init(43)
-    if geom == "b16d16":
+    if geom == "b16d16_f32":   # FP32 samples (not integers) through the same kernel
+        img = (img.astype(np.float32) + synth.make_image(47, 256, 256, u8=False)[None] * 0.25) * 0.8
+    if geom.startswith("b16d16"):
         cls, b, d = dict(C64, iters=0), 16, 16
     else:
         cls, b, d = dict(C32, iters=0), 8, 12
@@ -108,6 +110,14 @@ def test_learned_estimate_matches_network_oracle(P, geom):
         mask = synth.loss_mask(blocks, [8], 1, 256, 256)
     patches, _ = _learned(P, img, mask, blocks, cls, w, 0)
     x = np.stack([oimage.cnn_input(img[0], mask[0], int(bx), int(by), b, d) for _, bx, by, _c in blocks])
+    # the input's bf16 rounding is decided on the kernel's FP32 value s * (1/255)
+    # (the same decision on both sides; it matters for non-integer samples)
+    M = b + 2 * d
+    for i, (_, bx, by, _c) in enumerate(blocks):
+        ys = np.clip(np.arange(by - d, by - d + M), 0, img.shape[1] - 1)
+        xs = np.clip(np.arange(bx - d, bx - d + M), 0, img.shape[2] - 1)
+        s32 = img[0][np.ix_(ys, xs)].astype(np.float32) * np.float32(1.0 / 255.0)
+        x[i, 0] = np.where(x[i, 1] > 0, s32, 0.0)
     ref = 255.0 * ocnn.forward(w.astype(np.float64), x.astype(np.float32).astype(np.float64))
     ref_b = ref[:, d:d + b, d:d + b].reshape(len(blocks), -1)
     got = patches.reshape(len(blocks), -1).astype(np.float64)
@@ -176,3 +186,20 @@ def test_learned_without_weights_is_rejected(P):
         plain.load_init_weights(P.he_init(1))
     assert ei.value.status == 1
     plain.close()
+
+
+def test_argument_errors(P):
+    img, mask, blocks = _learned_scene()
+    dimg, dmask = torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda()
+    eng = P.Engine([C64])
+    short = torch.zeros((len(blocks), 47 * 47), dtype=torch.float32, device="cuda")
+    patches = torch.zeros(len(blocks) * 256, dtype=torch.float32, device="cuda")
+    with pytest.raises(P.FseError) as ei:       # estimate stride below M*M
+        eng.run_init(dimg, dmask, blocks, short, patches=patches)
+    assert ei.value.status == 1
+    eng.run(dimg, dmask, blocks, patches=patches)
+    with pytest.raises(P.FseError) as ei:       # area model needs a trace handle
+        eng.area_model()
+    assert ei.value.status == 1
+    eng.sync()
+    eng.close()
