@@ -178,18 +178,21 @@ __device__ __forceinline__ void gsync(const Grp &gr) {
     else __syncwarp(gr.amask);
 }
 
+// Maximum of a non-negative float over the group.  A maximum does not depend
+// on the order in which it is taken, so the result is the same for every
+// thread-to-bin mapping the autotuner may choose.
 template <int F, int PAIRS, int NT>
-__device__ __forceinline__ float group_sum(float v, const Grp &gr, RedShared *rs) {
+__device__ __forceinline__ float group_max(float v, const Grp &gr, RedShared *rs) {
     using G = Geo<F, PAIRS>;
 #pragma unroll
-    for (int o = G::LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gr.amask, v, o);
+    for (int o = G::LANES / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(gr.amask, v, o));
     if constexpr (G::TB > 32) {
         const int warp = threadIdx.x >> 5;
         if ((threadIdx.x & 31) == 0) rs->sum[warp] = v;
         gsync<F, PAIRS, NT>(gr);
         float t = 0.f;
 #pragma unroll
-        for (int i = 0; i < G::WPG; ++i) t += rs->sum[gr.g * G::WPG + i];
+        for (int i = 0; i < G::WPG; ++i) t = fmaxf(t, rs->sum[gr.g * G::WPG + i]);
         gsync<F, PAIRS, NT>(gr);
         return t;
     }
@@ -406,7 +409,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         sv[t] = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
                              : reinterpret_cast<const float *>(row)[xx];
     }
-    float sws2 = 0.f, sw = 0.f;
+    float smax = 0.f;
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
         const int pix = lt + t * TB;
@@ -420,19 +423,18 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         // warm start: the support holds the residual of the estimate
         const float sr = (inA && P.est != nullptr) ? sv[t] - P.est[blk.orig * P.est_stride + am * M + an] : sv[t];
         const float ws = w * sr;
-        sws2 = fmaf(ws, sr, sws2);
-        sw += w;
+        if (inA) smax = fmaxf(smax, fabsf(sr));
         Z[m * FP + n] = make_float2(ws, w);
     }
-    // alpha = power of two near the weighted RMS of s: balances the two real
-    // signals packed into one complex FFT (exact scaling)
-    const float tsw = group_sum<F, PAIRS, NT>(sw, gr, rsh);
-    const float tsws2 = group_sum<F, PAIRS, NT>(sws2, gr, rsh);
+    // alpha = the power of two in (max|s| / 2, max|s|] over the support:
+    // balances the two real signals packed into one complex FFT (an exact
+    // scaling; a maximum, so it is independent of the thread mapping)
+    const float tmaxs = group_max<F, PAIRS, NT>(smax, gr, rsh);
     float alpha = 1.f;
-    if (tsw > 0.f && tsws2 > 0.f) {
+    if (tmaxs > 0.f) {
         int e;
-        frexpf(sqrtf(tsws2 / tsw), &e);
-        alpha = ldexpf(1.f, e);
+        frexpf(tmaxs, &e);
+        alpha = ldexpf(1.f, e - 1);
     }
     for (int pix = lt; pix < F * F; pix += TB) {
         const int m = pix / F, n = pix % F;

@@ -7,8 +7,10 @@ device memory, a process that forbids allocation after start-up).  For them
 the library offers one entry point whose scratch is a fixed array inside the
 library.  This test calls it through the C ABI twice in a row, on two
 different batches, and checks each result against the handle-based entry
-point (fse_extrapolate_batch) on the same inputs, within the pixel tolerance
-of the parity tests; it also checks that an oversized batch is refused.
+point (fse_extrapolate_batch) on the same inputs, bit for bit: the kernel's
+arithmetic does not depend on the thread mapping, and on these small batches
+the handle path runs the 256-thread mapping while the allocation-free path
+runs the 128-thread one.  It also checks that an oversized batch is refused.
 The file name makes pytest collect it last.
 """
 import numpy as np
@@ -22,7 +24,6 @@ torch = pytest.importorskip("torch")
 C16 = dict(block=4, border=6, fft=16, rho=0.8, gamma=0.5, iters=120)
 C32 = dict(block=8, border=12, fft=32, rho=0.8, gamma=0.5, iters=120)
 C64 = dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=120)
-PIX_TOL = 1e-2
 
 
 def _batches():
@@ -54,7 +55,7 @@ def test_noalloc_matches_handle_entry_two_calls():
                                         blocks, len(blocks), got.data_ptr(), stream)
         torch.cuda.synchronize()
         diff = (got - ref).abs().max().item()
-        assert diff <= PIX_TOL, diff
+        assert diff == 0.0, diff
         assert torch.count_nonzero(got).item() > 0
 
 
