@@ -661,7 +661,7 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     size_t smem = 0;
     for (int c = 0; c < cfg->n_classes; ++c) {
         const int F = cfg->cls[c].fft;
-        smem = std::max(smem, (size_t)(4096 / (F * F)) * 16 * F * F);
+        smem = std::max(smem, (size_t)fse::cta_region_bytes(F));
     }
     h->smem_bytes = smem;
     CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -142,8 +142,18 @@ template <int F, int PAIRS>
 struct Geo {
     static constexpr int TB = F * F / (2 * PAIRS);   // threads per block
     static constexpr int LPR = F / 2;                // lanes per spectrum row
-    static constexpr int RSTEP = TB / LPR;           // row step between a thread's rows
-    static constexpr int REGION = 16 * F * F;        // smem bytes per block
+    static constexpr int RSTEP = TB / LPR;           // row groups of the block's threads
+    // F = 64: a thread's rows are runs of 8 consecutive rows, and W carries a
+    // copy of rows 0..6 after row F-1, so a shifted run never wraps (its 8
+    // loads address one base with immediate offsets).  Other sizes: rows
+    // r0, r0 + RSTEP, ... and one select per load at the wrap.
+    static constexpr bool RUNS = F == 64;
+    static constexpr int WROWS = RUNS ? F + 7 : F;   // W chunk rows in shared memory
+    static constexpr int REGION = RUNS ? 16 * F * WROWS : 16 * F * F;   // smem bytes per block
+    __device__ __forceinline__ static int row(int r0, int i) {   // spectrum row of pair i
+        if constexpr (RUNS) return (((i >> 3) * RSTEP + r0) << 3) + (i & 7);
+        else return r0 + i * RSTEP;
+    }
     static constexpr int FP = F + 1;                 // padded row of the FFT buffer
     static constexpr int R1 = (F == 16) ? 4 : 8;     // four-step FFT radices
     static constexpr int R2 = F / R1;
@@ -151,7 +161,13 @@ struct Geo {
     static constexpr int LANES = TB < 32 ? TB : 32;      // lanes per group and warp
     static constexpr int NQ = PAIRS / 4;                 // quartets of pairs
     static_assert(RSTEP * PAIRS == F, "thread rows must tile the spectrum");
+    static_assert(!RUNS || PAIRS % 8 == 0, "runs of 8 rows");
+    static_assert(REGION >= 8 * F * FP, "the FFT buffer fits the region");
 };
+
+// dynamic shared memory of one CTA working on blocks of FFT size F (one
+// F = 64 block, or 4096 / F^2 smaller blocks)
+__host__ __device__ constexpr int cta_region_bytes(int F) { return F == 64 ? 16 * 64 * (64 + 7) : 65536; }
 
 constexpr int kMaxWarps = 8;
 
@@ -307,7 +323,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
     const int c0 = gr.lt % G::LPR, r0 = gr.lt / G::LPR;
     auto lin = [&](int slot) -> uint32_t {      // slot -> linear bin index
         const int i = slot >> 1, h = slot & 1;
-        return (uint32_t)((r0 + i * G::RSTEP) * F + c0 + h * (F / 2));
+        return (uint32_t)(G::row(r0, i) * F + c0 + h * (F / 2));
     };
     const int lane = threadIdx.x & 31;
     Pick p;
@@ -456,7 +472,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     float4 Wc[PAIRS];
 #pragma unroll
     for (int i = 0; i < PAIRS; ++i) {
-        const int k = r0 + i * RSTEP, km = (F - k) & (F - 1);
+        const int k = G::row(r0, i), km = (F - k) & (F - 1);
         float2 R2[2], W2[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -468,7 +484,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         Rre[i] = pk(R2[0].x, R2[1].x);
         Rim[i] = pk(R2[0].y, R2[1].y);
         Wc[i] = make_float4(W2[0].x, W2[1].x, W2[0].y, W2[1].y);
-        if ((i + 1) * RSTEP > SAFE && k >= SAFE) {   // (first test is compile-time)
+        if (k >= SAFE) {
             Wd[k * F + c0] = Wc[i];
             Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
@@ -477,10 +493,14 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     gsync<F, PAIRS, NT>(gr);
 #pragma unroll
     for (int i = 0; i < PAIRS; ++i) {
-        const int k = r0 + i * RSTEP;
-        if (i * RSTEP < SAFE && k < SAFE) {
+        const int k = G::row(r0, i);
+        if (k < SAFE) {
             Wd[k * F + c0] = Wc[i];
             Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        }
+        if (G::RUNS && k < G::WROWS - F) {   // the copy of the first rows after row F-1
+            Wd[(k + F) * F + c0] = Wc[i];
+            Wd[(k + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     gsync<F, PAIRS, NT>(gr);
@@ -542,14 +562,20 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         }
         // ---- S8: R_w[k,l] -= c W[k-u, l-v] fused with |R_w|^2 and max ----
         const uint64_t ncr = pk(-cr, -cr), pci = pk(ci, ci), nci = pk(-ci, -ci);
-        // Row of pair i is (r0 - u + i*RSTEP) mod F: it wraps once, at pair iw.
-        // Pairs before the wrap address from A, the others from A - F*F, so each
-        // load needs one select and an immediate offset.
+        // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
+        // at pair iw.  Pairs before the wrap address from A, the others from
+        // A - F*F, so each load needs one select and an immediate offset.
+        // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
+        // contiguous in W (rows F.. repeat rows 0..6): one base per run.
         const int qcol = (c0 - v) & (F - 1);
         const int rb = (r0 - u) & (F - 1);
         const int iw = (F - rb + RSTEP - 1) / RSTEP;
         const ulonglong2 *A = Wq + rb * F + qcol;
         const ulonglong2 *A2 = A - F * F;
+        const ulonglong2 *Ar[G::RUNS ? PAIRS / 8 : 1];
+#pragma unroll
+        for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
+            Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
         tmax = 0.f;
 #pragma unroll
         for (int j = 0; j < NQ; ++j) {
@@ -558,7 +584,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             for (int ii = 0; ii < 4; ++ii) {
                 const int i = 4 * j + ii;
                 // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                const ulonglong2 w = (i < iw ? A : A2)[i * RSTEP * F];
+                const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                                             : (i < iw ? A : A2)[i * RSTEP * F];
                 const uint64_t wre = w.x, wim = w.y;
                 uint64_t a = fma2(ncr, wre, Rre[i]);
                 Rre[i] = fma2(pci, wim, a);

@@ -36,6 +36,7 @@ void fse_internal_set_global_error(const char *msg);   // fse_api.cu: text of fs
 namespace {
 
 constexpr int kNoallocMaxBlocks = 65536;
+constexpr int kNoallocSmem = fse::cta_region_bytes(64);   // the largest per-CTA region
 constexpr int kMaxM = 64;   // largest window edge M = b + 2d <= F <= 64
 
 // layout of the scratch array (byte offsets, each 256-byte aligned)
@@ -151,11 +152,11 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess || !p) return fail(FSE_ERR_CUDA, "noalloc: cudaGetSymbolAddress(g_scratch) failed");
-            if (cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536) !=
+            if (cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNoallocSmem) !=
                 cudaSuccess)
                 return fail(FSE_ERR_CUDA, "noalloc: cannot set the kernel's shared-memory size");
             int occ = 0, sms = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, 65536) !=
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, kNoallocSmem) !=
                     cudaSuccess ||
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ < 1)
                 return fail(FSE_ERR_CUDA, "noalloc: occupancy query failed");
@@ -241,7 +242,7 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
     noalloc_bucket_kernel<<<1, 32 * FSE_MAX_CLASSES, 0, stream>>>(d_raw, n_blocks, d_rec, d_starts, n_classes);
     noalloc_setup_kernel<<<1, 1, 0, stream>>>(d_counter);
     const int grid = std::max(1, std::min(items, ds.ctas_per_sm * ds.sm_count));
-    fse::fse_batch_kernel<128><<<grid, 128, 65536, stream>>>(P);
+    fse::fse_batch_kernel<128><<<grid, 128, kNoallocSmem, stream>>>(P);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return fail(FSE_ERR_CUDA, "noalloc: kernel launch failed");
     return FSE_OK;
