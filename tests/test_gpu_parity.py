@@ -283,3 +283,25 @@ def test_area_model_matches_guided_oracle(fse, uneven):
         off_p += b * b
     print("area model: worst |gpu - oracle|", worst)
     assert worst <= parity.PIX_TOL
+
+
+def test_no_support_gives_zero_model(fse):
+    """Every sample of the area lost (W[0,0] = 0): the model stays zero (the
+    reading the oracle takes too), so B receives 0, or the estimate with a
+    warm start."""
+    img = synth.make_image(61, 64, 64)[None]
+    mask = np.ones((1, 64, 64), np.uint8)
+    blocks = np.array([[0, 16, 16, 0], [0, 32, 32, 0]], np.int32)
+    patches, sel, _ = run_gpu(fse, [dict(C64, iters=20)], img, mask, blocks)
+    assert np.all(patches == 0.0)
+    for i, (_, x, y, _c) in enumerate(blocks):
+        s, w, off = oimage.area_inputs(img[0], mask[0], int(x), int(y), 16, 16, 64, 0.8)
+        assert not np.any(w > 0)
+        assert np.all(oracle.cfse(s, w, 0.5, 20).g == 0)
+    eng = fse.Engine([dict(C64, iters=20)])
+    est = torch.full((2, 48 * 48), 77.25, dtype=torch.float32, device="cuda")
+    out = torch.zeros(512, dtype=torch.float32, device="cuda")
+    eng.run_init(torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda(), blocks, est, patches=out)
+    eng.sync()
+    eng.close()
+    assert np.all(out.cpu().numpy() == 77.25)
