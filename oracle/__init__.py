@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The product library
 never imports this package, and this package never imports the product.
 
-The numerical kernels live in plain C (``fse_oracle.c``, ``cnn_oracle.c``),
+The numerical kernels live in plain C (``fse_oracle.c``, ``cnn_oracle.c``,
+``fse3_oracle.c`` for video volumes),
 compiled with gcc into ``liboracle.so`` beside them; this module wraps them
 with numpy arrays.  ``image`` holds the image-level driver (gather of the
 extrapolation area, Eq. (3) weighting, fill of the loss area).
@@ -19,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["fse_oracle.c", "cnn_oracle.c"]
+_SOURCES = ["fse_oracle.c", "cnn_oracle.c", "fse3_oracle.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -55,7 +56,14 @@ def _load():
                                         ip, ip, dp, dp, dp, dp, dp, dp, dp]
             lib.oracle_cfse_spatial.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double,
                                                 ctypes.c_int, ip, dp, dp, dp]
-            for name in ("oracle_fft2", "oracle_cfse", "oracle_cfse_spatial"):
+            lib.oracle_fft3.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
+            lib.oracle_weight3.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, u8p, dp]
+            lib.oracle_cfse3.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double, ctypes.c_int,
+                                         ip, ip, dp, dp, dp, dp]
+            lib.oracle_cfse3_spatial.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double,
+                                                 ctypes.c_int, ip, dp, dp]
+            for name in ("oracle_fft2", "oracle_cfse", "oracle_cfse_spatial", "oracle_fft3", "oracle_cfse3",
+                         "oracle_cfse3_spatial"):
                 getattr(lib, name).restype = ctypes.c_int
             if hasattr(lib, "oracle_conv3x3_fwd"):
                 from . import cnn as _cnn  # noqa: F401  (registers CNN prototypes)
@@ -180,3 +188,69 @@ def cfse_spatial(s: np.ndarray, w: np.ndarray, gamma: float, iters: int):
         raise ValueError("oracle_cfse_spatial: bad argument")
     return (sel[:I].copy(), (coef[0::2] + 1j * coef[1::2])[:I].copy(), crit[:I].copy(),
             (g[0::2] + 1j * g[1::2]).reshape(F, F))
+
+
+# ----------------------------------------------------------------- 3-D (video)
+def fft3(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Unnormalised 3-D DFT (forward sign e^{-j}) of an Ft x F x F array."""
+    x = np.asarray(x, dtype=np.complex128)
+    Ft, F = x.shape[0], x.shape[1]
+    assert x.shape == (Ft, F, F)
+    re = np.ascontiguousarray(x.real)
+    im = np.ascontiguousarray(x.imag)
+    if _load().oracle_fft3(Ft, F, _ptr(re), _ptr(im), 1 if inverse else -1) != 0:
+        raise ValueError("oracle_fft3: sizes must be powers of two")
+    return re + 1j * im
+
+
+def weight3(T: int, M: int, rho: float, support: np.ndarray) -> np.ndarray:
+    """Weighting function on a T x M x M volume (support != 0 marks A)."""
+    sup = np.ascontiguousarray(support, dtype=np.uint8)
+    assert sup.shape == (T, M, M)
+    w = np.zeros((T, M, M))
+    _load().oracle_weight3(T, M, float(rho), _ptr(sup, ctypes.c_uint8), _ptr(w))
+    return w
+
+
+def cfse3(s: np.ndarray, w: np.ndarray, gamma: float, iters: int,
+          forced: np.ndarray | None = None) -> CfseResult:
+    """Algorithm 1 on an Ft x F x F grid; bins indexed (t F + k) F + l.
+    Returns a CfseResult with g of shape (Ft, F, F); e_second, R and W are not
+    computed (None)."""
+    s_re, s_im = _split(s)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Ft, F = s_re.shape[0], s_re.shape[1]
+    assert s_re.shape == (Ft, F, F) and w.shape == (Ft, F, F)
+    I = int(iters)
+    sel = np.zeros(max(I, 1), np.int32)
+    coef = np.zeros(2 * max(I, 1))
+    e_sel = np.zeros(max(I, 1))
+    e_max = np.zeros(max(I, 1))
+    g = np.zeros(2 * Ft * F * F)
+    fp = None
+    if forced is not None:
+        fp = np.ascontiguousarray(forced, dtype=np.int32)
+        assert fp.shape[0] >= I
+    rc = _load().oracle_cfse3(Ft, F, _ptr(s_re), _ptr(s_im), _ptr(w), float(gamma), I, _ptr(fp, ctypes.c_int32),
+                              _ptr(sel, ctypes.c_int32), _ptr(coef), _ptr(e_sel), _ptr(e_max), _ptr(g))
+    if rc != 0:
+        raise ValueError("oracle_cfse3: bad argument")
+    return CfseResult(sel[:I].copy(), (coef[0::2] + 1j * coef[1::2])[:I].copy(), e_sel[:I].copy(),
+                      e_max[:I].copy(), None, (g[0::2] + 1j * g[1::2]).reshape(Ft, F, F), None, None)
+
+
+def cfse3_spatial(s: np.ndarray, w: np.ndarray, gamma: float, iters: int):
+    """Brute-force spatial-domain cFSE on an Ft x F x F grid; returns
+    (sel, coef, g)."""
+    s_re, s_im = _split(s)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Ft, F = s_re.shape[0], s_re.shape[1]
+    I = int(iters)
+    sel = np.zeros(max(I, 1), np.int32)
+    coef = np.zeros(2 * max(I, 1))
+    g = np.zeros(2 * Ft * F * F)
+    rc = _load().oracle_cfse3_spatial(Ft, F, _ptr(s_re), _ptr(s_im), _ptr(w), float(gamma), I,
+                                      _ptr(sel, ctypes.c_int32), _ptr(coef), _ptr(g))
+    if rc != 0:
+        raise ValueError("oracle_cfse3_spatial: bad argument")
+    return sel[:I].copy(), (coef[0::2] + 1j * coef[1::2])[:I].copy(), (g[0::2] + 1j * g[1::2]).reshape(Ft, F, F)

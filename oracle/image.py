@@ -17,7 +17,7 @@ import os
 
 import numpy as np
 
-from . import cfse, weight
+from . import cfse, cfse3, weight, weight3
 
 
 def area_inputs(img: np.ndarray, mask: np.ndarray, x: int, y: int, b: int, d: int,
@@ -119,3 +119,43 @@ def conceal(images: np.ndarray, mask: np.ndarray, blocks: np.ndarray, classes,
         out = list(ex.map(one, range(len(blocks))))
     patches = [p for p, _ in out]
     return patches, ([r for _, r in out] if keep_results else None)
+
+
+# ----------------------------------------------------------------- video volumes
+def area_inputs3(video, mask, t0, x, y, b, d, F, Ft, T, rho):
+    """Grid inputs of the 3-D extrapolation of the b x b block at (x, y) of
+    frame t0: the T x M x M volume of frames t0 - (T-1)/2 .. t0 + (T-1)/2
+    placed at offset ((Ft - T) // 2, (F - M) // 2, (F - M) // 2) of an
+    Ft x F x F grid.  Support: inside the video, not lost, not the block
+    itself (which is in the centre frame).  Returns (s_grid, w_grid, toff, off)."""
+    NF, H, W = video.shape
+    M = b + 2 * d
+    tc = (T - 1) // 2
+    sup = np.zeros((T, M, M), dtype=np.uint8)
+    svol = np.zeros((T, M, M))
+    for tau in range(T):
+        f = t0 - tc + tau
+        for m in range(M):
+            for n in range(M):
+                yy, xx = y - d + m, x - d + n
+                own = tau == tc and d <= m < d + b and d <= n < d + b
+                if 0 <= f < NF and 0 <= yy < H and 0 <= xx < W and not own and mask[f, yy, xx] == 0:
+                    sup[tau, m, n] = 1
+                    svol[tau, m, n] = float(video[f, yy, xx])
+    w = weight3(T, M, rho, sup)
+    toff, off = (Ft - T) // 2, (F - M) // 2
+    s_grid = np.zeros((Ft, F, F))
+    w_grid = np.zeros((Ft, F, F))
+    s_grid[toff:toff + T, off:off + M, off:off + M] = svol
+    w_grid[toff:toff + T, off:off + M, off:off + M] = w
+    return s_grid, w_grid, toff, off
+
+
+def conceal_block3(video, mask, t0, x, y, cls, forced=None):
+    """The 3-D oracle on one block; cls has block, border, fft, fft_t, frames,
+    rho, gamma, iters.  Returns (patch b x b, CfseResult)."""
+    b, d, F, Ft, T = cls["block"], cls["border"], cls["fft"], cls["fft_t"], cls["frames"]
+    s, w, toff, off = area_inputs3(video, mask, t0, x, y, b, d, F, Ft, T, cls["rho"])
+    res = cfse3(s, w, cls["gamma"], cls["iters"], forced=forced)
+    tc = toff + (T - 1) // 2
+    return res.g.real[tc, off + d:off + d + b, off + d:off + d + b], res
