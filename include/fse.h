@@ -69,6 +69,16 @@ typedef enum {
  *   gamma  orthogonality-deficiency compensation factor of Eq. (13),
  *          0 < gamma < 2 (the paper uses values in (0, 1])
  *   iters  I, number of selected basis functions (Algorithm 1), 0 <= I <= 4096
+ *   frames 0 or 1 for image areas.  3 for video volumes (Section II and the
+ *          Conclusion: the method extends to higher-dimensional data such as
+ *          video): the extrapolation volume is the M x M area in the block's
+ *          frame and in the frames before and after it (images[] is then a
+ *          sequence of frames; frames outside it are not support), the
+ *          weighting function's distance includes the frame offset, and
+ *          Algorithm 1 runs on a 4 x F x F transform grid (the volume in
+ *          planes 0..2) with 3-D basis functions and circular shifts.  Volume
+ *          classes need fft 16 or 32; they are not available with the learned
+ *          initialisation, fse_get_area_model or the allocation-free entry.
  */
 typedef struct {
     int block;
@@ -77,6 +87,7 @@ typedef struct {
     float rho;
     float gamma;
     int iters;
+    int frames;   /* 0 or 1: image areas; 3: video volumes (see below) */
 } fse_class;
 
 /*

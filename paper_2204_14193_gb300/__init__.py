@@ -31,7 +31,8 @@ STATUS = {0: "FSE_OK", 1: "FSE_ERR_INVALID_ARG", 2: "FSE_ERR_UNSUPPORTED", 3: "F
 
 class fse_class(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("border", ctypes.c_int), ("fft", ctypes.c_int),
-                ("rho", ctypes.c_float), ("gamma", ctypes.c_float), ("iters", ctypes.c_int)]
+                ("rho", ctypes.c_float), ("gamma", ctypes.c_float), ("iters", ctypes.c_int),
+                ("frames", ctypes.c_int)]
 
 
 class fse_config(ctypes.Structure):
@@ -174,7 +175,7 @@ def fse_extrapolate_batch_noalloc(classes, images: int, dtype: int, n_images: in
     ``blocks`` a host int32 [n, 4] array, the other buffers device pointers."""
     arr = (fse_class * len(classes))(*[
         fse_class(int(c["block"]), int(c["border"]), int(c["fft"]), float(c["rho"]), float(c["gamma"]),
-                  int(c["iters"])) for c in classes])
+                  int(c["iters"]), int(c.get("frames", 0))) for c in classes])
     blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
     st = _load().fse_extrapolate_batch_noalloc(arr, len(classes), images, dtype, n_images, height, width,
                                                pitch_bytes, loss_mask,
@@ -325,7 +326,7 @@ def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero
     cfg.n_classes = len(classes)
     for i, c in enumerate(classes):
         cfg.cls[i] = fse_class(int(c["block"]), int(c["border"]), int(c["fft"]), float(c["rho"]),
-                               float(c["gamma"]), int(c["iters"]))
+                               float(c["gamma"]), int(c["iters"]), int(c.get("frames", 0)))
     cfg.init = FSE_INIT_LEARNED if init == "learned" else FSE_INIT_ZERO
     cfg.init_iters = int(init_iters)
     cfg.device = device

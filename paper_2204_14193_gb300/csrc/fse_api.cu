@@ -176,12 +176,19 @@ fse_status validate_config(const fse_config *cfg) {
             return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: gamma %g not in (0, 2)", i, (double)c.gamma);
         if (c.iters < 0 || c.iters > 4096)
             return fail(nullptr, FSE_ERR_INVALID_ARG, "class %d: iters %d not in [0, 4096]", i, c.iters);
+        if (c.frames < 0 || c.frames == 2 || c.frames > 3)
+            return fail(nullptr, c.frames > 3 ? FSE_ERR_UNSUPPORTED : FSE_ERR_INVALID_ARG,
+                        "class %d: frames %d (0 or 1: images, 3: video volumes)", i, c.frames);
+        if (c.frames == 3 && c.fft == 64)
+            return fail(nullptr, FSE_ERR_UNSUPPORTED, "class %d: video volumes need fft 16 or 32", i);
     }
     if (cfg->init != FSE_INIT_ZERO && cfg->init != FSE_INIT_LEARNED)
         return fail(nullptr, FSE_ERR_INVALID_ARG, "init mode %d unknown", cfg->init);
     if (cfg->init == FSE_INIT_LEARNED) {
         if (cfg->n_classes != 1)
             return fail(nullptr, FSE_ERR_UNSUPPORTED, "learned initialisation supports one block class per handle");
+        if (cfg->cls[0].frames > 1)
+            return fail(nullptr, FSE_ERR_UNSUPPORTED, "learned initialisation is for image areas");
         if (cfg->init_iters < 0 || cfg->init_iters > 4096)
             return fail(nullptr, FSE_ERR_INVALID_ARG, "init_iters %d not in [0, 4096]", cfg->init_iters);
     }
@@ -247,7 +254,7 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         start[c] = pos;
         if (cnt[c] == 0) continue;
         const int F = cfg.cls[c].fft;
-        const int bpi = 4096 / (F * F);
+        const int bpi = 4096 / (F * F * (cfg.cls[c].frames > 1 ? 4 : 1));
         items += (cnt[c] + bpi - 1) / bpi;
         pl.seg_cls[pl.n_seg] = c;
         pl.seg_item_end[pl.n_seg] = items;
@@ -581,10 +588,15 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         D.M = k.block + 2 * k.border;
         D.off = (k.fft - D.M) / 2;
         D.iters = (learned && h->cfg.init_iters > 0) ? h->cfg.init_iters : k.iters;
-        D.bpi = 4096 / (k.fft * k.fft);
+        D.FT = k.frames > 1 ? 4 : 1;
+        D.T = k.frames > 1 ? k.frames : 1;
+        D.tc = (D.T - 1) / 2;
+        D.toff = (D.FT - D.T) / 2;
+        D.bpi = 4096 / (k.fft * k.fft * D.FT);
         D.gamma = k.gamma;
         D.wtab = h->d_wtab[c];
     }
+    P.n_images = n_images;
     P.counter = h->d_counter;
     P.tr_sel = trace ? h->d_tr_sel : nullptr;
     P.tr_energy = trace ? h->d_tr_energy : nullptr;
@@ -690,9 +702,10 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     CREATE_CUDA(cudaGetLastError());
     for (int c = 0; c < cfg->n_classes; ++c) {
         const int M = cfg->cls[c].block + 2 * cfg->cls[c].border;
-        CREATE_CUDA(cudaMalloc(&h->d_wtab[c], (size_t)M * M * sizeof(float)));
-        fse::weight_table_kernel<<<(M * M + 255) / 256, 256, 0, h->cap_stream>>>(h->d_wtab[c], M,
-                                                                                (double)cfg->cls[c].rho);
+        const int T = cfg->cls[c].frames > 1 ? cfg->cls[c].frames : 1;
+        CREATE_CUDA(cudaMalloc(&h->d_wtab[c], (size_t)T * M * M * sizeof(float)));
+        fse::weight_table_kernel<<<(T * M * M + 255) / 256, 256, 0, h->cap_stream>>>(h->d_wtab[c], M, T,
+                                                                                    (double)cfg->cls[c].rho);
         CREATE_CUDA(cudaGetLastError());
     }
     CREATE_CUDA(cudaStreamSynchronize(h->cap_stream));
@@ -823,6 +836,8 @@ fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, 
         maxMM = std::max(maxMM, M * M);
     }
     if (model_stride < maxMM) return fail(h, FSE_ERR_INVALID_ARG, "model_stride %zu < largest area %zu", model_stride, maxMM);
+    for (int c = 0; c < h->cfg.n_classes; ++c)
+        if (h->cfg.cls[c].frames > 1) return fail(h, FSE_ERR_UNSUPPORTED, "the area model is for image classes");
     if (h->last_n_blocks == 0) return FSE_OK;
     if (!model) return fail(h, FSE_ERR_INVALID_ARG, "model is NULL");
     DeviceGuard guard(h->device);

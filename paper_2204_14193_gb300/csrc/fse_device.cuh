@@ -30,9 +30,13 @@ namespace fse {
 constexpr int kMaxClasses = 4;
 
 struct DevClass {
-    int F, b, d, M, off, iters, bpi;  // bpi: blocks per work item (4096 / F^2)
+    int F, b, d, M, off, iters, bpi;  // bpi: blocks per work item (4096 / (FT F^2))
     float gamma;
-    const float *wtab;                // M*M Eq. (3) weights
+    const float *wtab;                // T*M*M weights (Eq. (3), extended by the frame offset)
+    int FT = 1;                       // temporal transform size (1: images; 4: video volumes)
+    int T = 1;                        // frames of the volume (odd), centred on the block's frame
+    int tc = 0;                       // the block's frame in the volume, (T - 1) / 2
+    int toff = 0;                     // first grid plane of the volume, (FT - T) / 2
 };
 
 struct BlockRec {                     // one lost block, in queue order
@@ -44,6 +48,7 @@ struct BlockRec {                     // one lost block, in queue order
 struct DevParams {
     const void *images;
     int dtype;                        // 0 = u8, 1 = f32
+    int n_images;                     // frames of a video (support of volume classes)
     int H, W;
     long long pitch;                  // bytes per image row
     const uint8_t *mask;
@@ -138,18 +143,18 @@ __device__ __forceinline__ void dftR(float2 *x) {
 // holds NT / TB = 4096 / F^2 blocks whatever NT is.
 //   NT = 128 (16 pairs): F=64 -> 4 warps, F=32 -> 1 warp, F=16 -> 8 lanes
 //   NT = 256 ( 8 pairs): F=64 -> 8 warps, F=32 -> 2 warps, F=16 -> 16 lanes
-template <int F, int PAIRS>
+template <int F, int PAIRS, int FT = 1>
 struct Geo {
-    static constexpr int TB = F * F / (2 * PAIRS);   // threads per block
+    static constexpr int TB = FT * F * F / (2 * PAIRS);   // threads per block
     static constexpr int LPR = F / 2;                // lanes per spectrum row
     static constexpr int RSTEP = TB / LPR;           // row groups of the block's threads
     // F = 64: a thread's rows are runs of 8 consecutive rows, and W carries a
     // copy of rows 0..6 after row F-1, so a shifted run never wraps (its 8
     // loads address one base with immediate offsets).  Other sizes: rows
     // r0, r0 + RSTEP, ... and one select per load at the wrap.
-    static constexpr bool RUNS = F == 64;
+    static constexpr bool RUNS = F == 64 && FT == 1;
     static constexpr int WROWS = RUNS ? F + 7 : F;   // W chunk rows in shared memory
-    static constexpr int REGION = RUNS ? 16 * F * WROWS : 16 * F * F;   // smem bytes per block
+    static constexpr int REGION = RUNS ? 16 * F * WROWS : 16 * F * F * FT;   // smem bytes per block
     __device__ __forceinline__ static int row(int r0, int i) {   // spectrum row of pair i
         if constexpr (RUNS) return (((i >> 3) * RSTEP + r0) << 3) + (i & 7);
         else return r0 + i * RSTEP;
@@ -160,9 +165,10 @@ struct Geo {
     static constexpr int WPG = TB >= 32 ? TB / 32 : 1;   // warps per group
     static constexpr int LANES = TB < 32 ? TB : 32;      // lanes per group and warp
     static constexpr int NQ = PAIRS / 4;                 // quartets of pairs
-    static_assert(RSTEP * PAIRS == F, "thread rows must tile the spectrum");
+    static_assert(RSTEP * PAIRS == FT * F, "thread rows must tile the spectrum");
+    static_assert(FT == 1 || F % RSTEP == 0, "a thread's rows repeat in every temporal plane");
     static_assert(!RUNS || PAIRS % 8 == 0, "runs of 8 rows");
-    static_assert(REGION >= 8 * F * FP, "the FFT buffer fits the region");
+    static_assert(REGION >= 8 * FT * F * FP, "the FFT buffer fits the region");
 };
 
 // dynamic shared memory of one CTA working on blocks of FFT size F (one
@@ -186,9 +192,9 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <int F, int PAIRS, int NT>
+template <int F, int PAIRS, int NT, int FT = 1>
 __device__ __forceinline__ void gsync(const Grp &gr) {
-    using G = Geo<F, PAIRS>;
+    using G = Geo<F, PAIRS, FT>;
     if constexpr (G::TB == NT) __syncthreads();
     else if constexpr (G::TB > 32) named_barrier(1 + gr.g, G::TB);
     else __syncwarp(gr.amask);
@@ -197,19 +203,19 @@ __device__ __forceinline__ void gsync(const Grp &gr) {
 // Maximum of a non-negative float over the group.  A maximum does not depend
 // on the order in which it is taken, so the result is the same for every
 // thread-to-bin mapping the autotuner may choose.
-template <int F, int PAIRS, int NT>
+template <int F, int PAIRS, int NT, int FT = 1>
 __device__ __forceinline__ float group_max(float v, const Grp &gr, RedShared *rs) {
-    using G = Geo<F, PAIRS>;
+    using G = Geo<F, PAIRS, FT>;
 #pragma unroll
     for (int o = G::LANES / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(gr.amask, v, o));
     if constexpr (G::TB > 32) {
         const int warp = threadIdx.x >> 5;
         if ((threadIdx.x & 31) == 0) rs->sum[warp] = v;
-        gsync<F, PAIRS, NT>(gr);
+        gsync<F, PAIRS, NT, FT>(gr);
         float t = 0.f;
 #pragma unroll
         for (int i = 0; i < G::WPG; ++i) t = fmaxf(t, rs->sum[gr.g * G::WPG + i]);
-        gsync<F, PAIRS, NT>(gr);
+        gsync<F, PAIRS, NT, FT>(gr);
         return t;
     }
     return v;
@@ -223,48 +229,70 @@ __device__ __forceinline__ float group_max(float v, const Grp &gr, RedShared *rs
 //   step 2: for each (line, k1): DFT_R2 over n2 of the values at R2 k1 + n2,
 //           stored at k1 + R1 k2 (all loads before all stores).
 // ROWS selects rows (element stride 1) or columns (element stride FP).
-template <int F, int PAIRS, int NT, bool ROWS>
+template <int F, int PAIRS, int NT, bool ROWS, int FT = 1>
 __device__ __forceinline__ void fft_pass(float2 *Z, const float2 *s_tw, const Grp &gr) {
-    using G = Geo<F, PAIRS>;
+    using G = Geo<F, PAIRS, FT>;
     constexpr int TB = G::TB, R1 = G::R1, R2 = G::R2, FP = G::FP;
-    constexpr int LS = ROWS ? FP : 1;     // line stride
+    constexpr int LS = ROWS ? FP : 1;     // line stride within a plane
     constexpr int ES = ROWS ? 1 : FP;     // element stride
-    constexpr int N1 = F * R2 / TB;       // step-1 tasks per thread
-    constexpr int N2 = F * R1 / TB;       // step-2 tasks per thread
-    static_assert(N1 * TB == F * R2 && N2 * TB == F * R1, "FFT tasks must tile the group");
+    constexpr int NL = FT * F;            // lines over all FT planes of F x FP
+    constexpr int N1 = NL * R2 / TB;      // step-1 tasks per thread
+    constexpr int N2 = NL * R1 / TB;      // step-2 tasks per thread
+    static_assert(N1 * TB == NL * R2 && N2 * TB == NL * R1, "FFT tasks must tile the group");
+    // line L of plane L / F: offset (L / F) F FP + (L % F) LS
+    auto lbase = [](int L) { return (L / F) * F * FP + (L % F) * LS; };
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
         const int t = gr.lt + j * TB;
-        const int line = t % F, n2 = t / F;
+        const int line = lbase(t % NL), n2 = t / NL;
         float2 x[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) x[n1] = Z[line * LS + (R2 * n1 + n2) * ES];
+        for (int n1 = 0; n1 < R1; ++n1) x[n1] = Z[line + (R2 * n1 + n2) * ES];
         dftR<R1>(x);
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) {
             const float2 tw = s_tw[((n2 * k1) * (64 / F)) & 63];
-            Z[line * LS + (R2 * k1 + n2) * ES] = cmul_conj_tw(x[k1], tw);
+            Z[line + (R2 * k1 + n2) * ES] = cmul_conj_tw(x[k1], tw);
         }
     }
-    gsync<F, PAIRS, NT>(gr);
+    gsync<F, PAIRS, NT, FT>(gr);
     float2 y[N2][R2];
 #pragma unroll
     for (int j = 0; j < N2; ++j) {
         const int t = gr.lt + j * TB;
-        const int line = t % F, k1 = t / F;
+        const int line = lbase(t % NL), k1 = t / NL;
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) y[j][n2] = Z[line * LS + (R2 * k1 + n2) * ES];
+        for (int n2 = 0; n2 < R2; ++n2) y[j][n2] = Z[line + (R2 * k1 + n2) * ES];
         dftR<R2>(y[j]);
     }
-    gsync<F, PAIRS, NT>(gr);
+    gsync<F, PAIRS, NT, FT>(gr);
 #pragma unroll
     for (int j = 0; j < N2; ++j) {
         const int t = gr.lt + j * TB;
-        const int line = t % F, k1 = t / F;
+        const int line = lbase(t % NL), k1 = t / NL;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) Z[line * LS + (k1 + R1 * k2) * ES] = y[j][k2];
+        for (int k2 = 0; k2 < R2; ++k2) Z[line + (k1 + R1 * k2) * ES] = y[j][k2];
     }
-    gsync<F, PAIRS, NT>(gr);
+    gsync<F, PAIRS, NT, FT>(gr);
+}
+
+// The temporal pass of a volume's transform (FT = 4): for every spatial bin,
+// the length-4 DFT across the four planes (exact: the twiddles are +-1, +-j).
+template <int F, int PAIRS, int NT, int FT>
+__device__ __forceinline__ void time_pass(float2 *Z, const Grp &gr) {
+    using G = Geo<F, PAIRS, FT>;
+    constexpr int TB = G::TB, FP = G::FP, PS = F * FP;   // plane stride
+    static_assert(FT == 4, "temporal transform of length 4");
+    static_assert(F * F % TB == 0, "tasks tile the group");
+#pragma unroll
+    for (int j = 0; j < F * F / TB; ++j) {
+        const int q = gr.lt + j * TB;
+        float2 *z = Z + (q / F) * FP + (q % F);
+        float2 x0 = z[0], x1 = z[PS], x2 = z[2 * PS], x3 = z[3 * PS];
+        dft4(x0, x1, x2, x3);
+        z[0] = x0; z[PS] = x1; z[2 * PS] = x2; z[3 * PS] = x3;
+    }
+    gsync<F, PAIRS, NT, FT>(gr);
 }
 
 // ------------------------------------------------------- argmax reduction
@@ -315,10 +343,10 @@ __device__ __forceinline__ int thread_search(const uint64_t *Rre, const uint64_t
 // so the reduction is built from as few DEPENDENT such steps as possible:
 // one redux.sync for the max, the owner's register search, one redux.sync for
 // the smallest index, and (multi-warp groups) one shared-memory exchange.
-template <int F, int PAIRS, int NT>
+template <int F, int PAIRS, int NT, int FT = 1>
 __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t *Rim, float tmax,
                                              const float *q, const Grp &gr, RedShared *rs, int parity) {
-    using G = Geo<F, PAIRS>;
+    using G = Geo<F, PAIRS, FT>;
     const uint32_t mt = __float_as_uint(tmax);
     const int c0 = gr.lt % G::LPR, r0 = gr.lt / G::LPR;
     auto lin = [&](int slot) -> uint32_t {      // slot -> linear bin index
@@ -343,7 +371,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         uint4 *win = rs->win[parity];
         if ((cand == iw && cand != 0xffffffffu) || (iw == 0xffffffffu && lane == 0))
             win[warp] = make_uint4(mw, iw, __float_as_uint(rr), __float_as_uint(ri));
-        gsync<F, PAIRS, NT>(gr);
+        gsync<F, PAIRS, NT, FT>(gr);
         p.idx = 0xffffffffu; p.rr = 0.f; p.ri = 0.f; p.ebits = 0u;
 #pragma unroll
         for (int i = 0; i < G::WPG; ++i) {
@@ -389,11 +417,14 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 
 // ------------------------------------------------------- per-block worker
 // NP: B samples per thread (compile time; the caller picks the smallest
-// variant that covers b*b).
-template <int F, int PAIRS, int NT, int NP>
+// variant that covers b*b).  FT: temporal transform size (1: an image area;
+// 4: a video volume of C.T frames centred on the block's frame, transform
+// grid FT x F x F with bins indexed (t F + k) F + l -- the same Algorithm 1
+// with 3-D basis functions and 3-D circular shifts).
+template <int F, int PAIRS, int NT, int NP, int FT = 1>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
-    using G = Geo<F, PAIRS>;
+    using G = Geo<F, PAIRS, FT>;
     constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
     Grp gr;
     gr.g = threadIdx.x / TB;
@@ -412,16 +443,20 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     // All loads of the thread's grid positions are issued first (clamped to
     // the image, so always in bounds), then the weights are applied: one
     // memory round trip instead of one per position.
-    constexpr int NPOS = F * F / TB;
+    constexpr int NPOS = FT * F * F / TB;
     float sv[NPOS];
     uint8_t mk[NPOS];
+    // volume plane t holds frame blk.image + t - toff - tc (clamped for the
+    // load; frames outside the video are not support)
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
         const int pix = lt + t * TB;
-        const int yy = min(max(blk.y - d + pix / F - off, 0), P.H - 1);
-        const int xx = min(max(blk.x - d + pix % F - off, 0), P.W - 1);
-        mk[t] = P.mask[((size_t)blk.image * P.H + yy) * P.W + xx];
-        const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+        const int pl = pix / (F * F), pp = pix % (F * F);
+        const int fr = FT == 1 ? blk.image : min(max(blk.image + pl - C.toff - C.tc, 0), P.n_images - 1);
+        const int yy = min(max(blk.y - d + pp / F - off, 0), P.H - 1);
+        const int xx = min(max(blk.x - d + pp % F - off, 0), P.W - 1);
+        mk[t] = P.mask[((size_t)fr * P.H + yy) * P.W + xx];
+        const char *row = static_cast<const char *>(P.images) + ((long long)fr * P.H + yy) * P.pitch;
         sv[t] = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
                              : reinterpret_cast<const float *>(row)[xx];
     }
@@ -429,50 +464,58 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
         const int pix = lt + t * TB;
-        const int m = pix / F, n = pix % F;
+        const int pl = pix / (F * F), pp = pix % (F * F);
+        const int m = pp / F, n = pp % F;
         const int am = m - off, an = n - off;
         const int yy = blk.y - d + am, xx = blk.x - d + an;
-        const bool inA = am >= 0 && am < M && an >= 0 && an < M &&
-                         !(am >= d && am < d + b && an >= d && an < d + b) &&
-                         yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0;
-        const float w = inA ? __ldg(&C.wtab[am * M + an]) : 0.f;
+        const int tau = pl - C.toff;                       // frame of the volume (FT = 1: 0)
+        const int fr = blk.image + tau - C.tc;
+        const bool own = tau == C.tc && am >= d && am < d + b && an >= d && an < d + b;
+        const bool inA = am >= 0 && am < M && an >= 0 && an < M && !own &&
+                         yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0 &&
+                         (FT == 1 || (tau >= 0 && tau < C.T && fr >= 0 && fr < P.n_images));
+        const float w = inA ? __ldg(&C.wtab[(FT == 1 ? 0 : tau * M * M) + am * M + an]) : 0.f;
         // warm start: the support holds the residual of the estimate
         const float sr = (inA && P.est != nullptr) ? sv[t] - P.est[blk.orig * P.est_stride + am * M + an] : sv[t];
         const float ws = w * sr;
         if (inA) smax = fmaxf(smax, fabsf(sr));
-        Z[m * FP + n] = make_float2(ws, w);
+        Z[(pl * F + m) * FP + n] = make_float2(ws, w);
     }
     // alpha = the power of two in (max|s| / 2, max|s|] over the support:
     // balances the two real signals packed into one complex FFT (an exact
     // scaling; a maximum, so it is independent of the thread mapping)
-    const float tmaxs = group_max<F, PAIRS, NT>(smax, gr, rsh);
+    const float tmaxs = group_max<F, PAIRS, NT, FT>(smax, gr, rsh);
     float alpha = 1.f;
     if (tmaxs > 0.f) {
         int e;
         frexpf(tmaxs, &e);
         alpha = ldexpf(1.f, e - 1);
     }
-    for (int pix = lt; pix < F * F; pix += TB) {
-        const int m = pix / F, n = pix % F;
-        Z[m * FP + n].y *= alpha;
+    for (int pix = lt; pix < FT * F * F; pix += TB) {
+        const int r = pix / F, n = pix % F;                 // r: plane * F + row
+        Z[r * FP + n].y *= alpha;
     }
-    gsync<F, PAIRS, NT>(gr);
-    // ---- S2/S3: FFT2 of z ----
-    fft_pass<F, PAIRS, NT, true>(Z, s_tw, gr);
-    fft_pass<F, PAIRS, NT, false>(Z, s_tw, gr);
+    gsync<F, PAIRS, NT, FT>(gr);
+    // ---- S2/S3: FFT2 of z (and the temporal pass of a volume) ----
+    fft_pass<F, PAIRS, NT, true, FT>(Z, s_tw, gr);
+    fft_pass<F, PAIRS, NT, false, FT>(Z, s_tw, gr);
+    if constexpr (FT > 1) time_pass<F, PAIRS, NT, FT>(Z, gr);
 
     // ---- split into R_w = FFT{w s} and W = FFT{w} ----
-    // W chunk rows k >= F/2 + 1 lie beyond the padded FFT buffer, so they are
+    // W chunk rows k >= SAFE lie beyond the padded FFT buffer, so they are
     // written at once; the others are held until every thread has read Z.
+    // (Rows are plane * F + row for a volume; the mirror bin of (t, k, l) is
+    // (-t, -k, -l).)
     const int c0 = lt % LPR, r0 = lt / LPR;
     const float ainv = 1.f / alpha;
     float4 *Wd = reinterpret_cast<float4 *>(region);
-    constexpr int SAFE = F / 2 + 1;
+    constexpr int SAFE = (FT * FP + 1) / 2;                // ceil(FT F FP 8 / (F 16))
     uint64_t Rre[PAIRS], Rim[PAIRS];
     float4 Wc[PAIRS];
 #pragma unroll
     for (int i = 0; i < PAIRS; ++i) {
-        const int k = G::row(r0, i), km = (F - k) & (F - 1);
+        const int k = G::row(r0, i);
+        const int km = (((FT - k / F) & (FT - 1)) * F) + ((F - k % F) & (F - 1));   // mirror row
         float2 R2[2], W2[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -490,7 +533,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         }
     }
     const float W00 = Z[0].y * ainv;
-    gsync<F, PAIRS, NT>(gr);
+    gsync<F, PAIRS, NT, FT>(gr);
 #pragma unroll
     for (int i = 0; i < PAIRS; ++i) {
         const int k = G::row(r0, i);
@@ -503,7 +546,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             Wd[(k + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
-    gsync<F, PAIRS, NT>(gr);
+    gsync<F, PAIRS, NT, FT>(gr);
 
     // ---- B samples owned by this thread (NP of them; samples j >= b*b are
     //      computed but never stored) ----
@@ -533,13 +576,16 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     }
     const int iters = C.iters;
     Pick pick;
-    if (iters > 0) pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, 0);
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, q, gr, rsh, 0);
 
     const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
     for (int nu = 1; nu <= iters; ++nu) {
         // ---- S6/S7: coefficient and model ----
         const float cr = pick.rr * cg, ci = pick.ri * cg;
-        const int u = (int)(pick.idx / F), v = (int)(pick.idx % F);
+        const int u = (int)((pick.idx / F) % F), v = (int)(pick.idx % F);
+        const int wt = FT == 1 ? 0 : (int)(pick.idx / (F * F));   // temporal frequency
+        // the temporal part of the phase on B's plane, in 64ths of a turn
+        const int tphase = FT == 1 ? 0 : (wt * (C.toff + C.tc) * (64 / FT)) & 63;
         if (P.tr_sel != nullptr && lt == 0) {
             const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
             P.tr_sel[o] = (int)pick.idx;
@@ -551,8 +597,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         auto model = [&]() {
 #pragma unroll
             for (int t = 0; t < NP; ++t) {
-                const int ph = (u * pm_[t] + v * pn_[t]) & (F - 1);
-                const float2 tw = s_tw[ph * (64 / F)];
+                const int ph = ((u * pm_[t] + v * pn_[t]) * (64 / F) + tphase) & 63;
+                const float2 tw = s_tw[ph];
                 acc[t] = fmaf(cr, tw.x, fmaf(-ci, tw.y, acc[t]));
             }
         };
@@ -576,6 +622,15 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
 #pragma unroll
         for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
             Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+        // Volumes: pair i lies in plane i / KP at row r0 + (i % KP) RSTEP; its
+        // shifted chunk is plane (i / KP - wt) mod FT, row (r0 + (i % KP) RSTEP
+        // - u) mod F: KP row offsets and FT plane offsets per iteration.
+        constexpr int KP = FT == 1 ? 1 : F / RSTEP;
+        int kofs[KP], tofs[FT];
+#pragma unroll
+        for (int j2 = 0; j2 < KP; ++j2) kofs[j2] = ((r0 + j2 * RSTEP - u) & (F - 1)) * F + qcol;
+#pragma unroll
+        for (int p2 = 0; p2 < FT; ++p2) tofs[p2] = ((p2 - wt) & (FT - 1)) * F * F;
         tmax = 0.f;
 #pragma unroll
         for (int j = 0; j < NQ; ++j) {
@@ -584,8 +639,9 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             for (int ii = 0; ii < 4; ++ii) {
                 const int i = 4 * j + ii;
                 // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
-                                             : (i < iw ? A : A2)[i * RSTEP * F];
+                const ulonglong2 w = FT > 1    ? Wq[tofs[i / KP] + kofs[i % KP]]
+                                     : G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                                               : (i < iw ? A : A2)[i * RSTEP * F];
                 const uint64_t wre = w.x, wim = w.y;
                 uint64_t a = fma2(ncr, wre, Rre[i]);
                 Rre[i] = fma2(pci, wim, a);
@@ -602,7 +658,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         }
         model();
         // ---- S5: next selection ----
-        pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, nu & 1);
+        pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, q, gr, rsh, nu & 1);
     }
 
     // ---- S10: write Re{g} on B ----
@@ -619,14 +675,21 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     }
 }
 
-template <int F, int PAIRS, int NT>
+template <int F, int PAIRS, int NT, int FT = 1>
 __device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
                                               unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
-    constexpr int TB = Geo<F, PAIRS>::TB;
-    constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
-    constexpr int NPL = PAIRS / 2;                // covers b <= F/2
-    if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS>(P, C, first, count, smem, s_tw, rsh);
-    else process<F, PAIRS, NT, NPL>(P, C, first, count, smem, s_tw, rsh);
+    constexpr int TB = Geo<F, PAIRS, FT>::TB;
+    if constexpr (FT == 1) {
+        constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
+        constexpr int NPL = PAIRS / 2;                // covers b <= F/2
+        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS>(P, C, first, count, smem, s_tw, rsh);
+        else process<F, PAIRS, NT, NPL>(P, C, first, count, smem, s_tw, rsh);
+    } else {
+        // a volume's block group is FT times larger: b <= F/2 needs
+        // F^2/4 / TB = PAIRS / (2 FT) samples per thread (at least 1)
+        constexpr int NPV = PAIRS / (2 * FT) > 0 ? PAIRS / (2 * FT) : 1;
+        process<F, PAIRS, NT, NPV, FT>(P, C, first, count, smem, s_tw, rsh);
+    }
 }
 
 // ------------------------------------------------------ persistent kernel
@@ -652,22 +715,29 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
         const DevClass &C = P.cls[P.seg_cls[sg]];
         const int first = P.seg_block_start[sg] + (item - item0) * C.bpi;
         const int count = min(C.bpi, P.seg_block_start[sg] + P.seg_block_count[sg] - first);
-        switch (C.F) {
-            case 64: process_class<64, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
-            case 32: process_class<32, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
-            default: process_class<16, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+        if (C.FT == 4) {
+            if (C.F == 32) process_class<32, PAIRS, NT, 4>(P, C, first, count, smem, s_tw, &rsh);
+            else process_class<16, PAIRS, NT, 4>(P, C, first, count, smem, s_tw, &rsh);
+        } else {
+            switch (C.F) {
+                case 64: process_class<64, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+                case 32: process_class<32, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+                default: process_class<16, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+            }
         }
         __syncthreads();
     }
 }
 
-// Eq. (3) weight table of one class, evaluated in FP64 and rounded once.
-__global__ void weight_table_kernel(float *wtab, int M, double rho) {
+// Eq. (3) weight table of one class, evaluated in FP64 and rounded once; for
+// a volume of T frames the distance includes the frame offset from the
+// centre frame (T = 1: the area's table).
+__global__ void weight_table_kernel(float *wtab, int M, int T, double rho) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M * M) return;
-    const int m = i / M, n = i % M;
-    const double cm = 0.5 * (M - 1);
-    const double dist = sqrt((m - cm) * (m - cm) + (n - cm) * (n - cm));
+    if (i >= T * M * M) return;
+    const int tau = i / (M * M), m = (i / M) % M, n = i % M;
+    const double cm = 0.5 * (M - 1), ct = 0.5 * (T - 1);
+    const double dist = sqrt((tau - ct) * (tau - ct) + (m - cm) * (m - cm) + (n - cm) * (n - cm));
     wtab[i] = (float)pow(rho, dist);
 }
 

@@ -115,6 +115,7 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
             return fail(FSE_ERR_INVALID_ARG, "noalloc: need 1 <= b <= fft/2, d >= 1, b + 2d <= fft");
         if (!(k.rho > 0.f && k.rho <= 1.f) || !(k.gamma > 0.f && k.gamma < 2.f) || k.iters < 0 || k.iters > 4096)
             return fail(FSE_ERR_INVALID_ARG, "noalloc: rho, gamma or iters out of range");
+        if (k.frames > 1) return fail(FSE_ERR_UNSUPPORTED, "noalloc: video volumes need fse_extrapolate_batch");
     }
     if (n_blocks < 0) return fail(FSE_ERR_INVALID_ARG, "noalloc: n_blocks < 0");
     if (n_blocks > kNoallocMaxBlocks)
@@ -196,6 +197,7 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
     P.total_items = items;
     P.images = images;
     P.dtype = dtype;
+    P.n_images = n_images;
     P.H = height;
     P.W = width;
     P.pitch = (long long)pitch_bytes;
@@ -226,7 +228,7 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
     fse::twiddle_kernel<<<1, 64, 0, stream>>>(d_tw);
     for (int c = 0; c < n_classes; ++c) {
         const int M = P.cls[c].M;
-        fse::weight_table_kernel<<<(M * M + 255) / 256, 256, 0, stream>>>(d_wtab + (size_t)c * kMaxM * kMaxM, M,
+        fse::weight_table_kernel<<<(M * M + 255) / 256, 256, 0, stream>>>(d_wtab + (size_t)c * kMaxM * kMaxM, M, 1,
                                                                           (double)classes[c].rho);
     }
     if (cudaMemcpyAsync(d_raw, blocks, (size_t)n_blocks * sizeof(fse_block), cudaMemcpyHostToDevice, stream) !=

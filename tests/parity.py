@@ -101,6 +101,53 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
     return out
 
 
+def mirror3(sel, Ft, F):
+    sel = np.asarray(sel, dtype=np.int64)
+    t, k, l = sel // (F * F), (sel // F) % F, sel % F
+    return ((((-t) % Ft) * F + ((-k) % F)) * F) + ((-l) % F)
+
+
+def check_block3(video, mask, blk, cls, gpu_patch, gpu_sel, gpu_energy):
+    """The criteria of check_block for a video-volume class (3-D oracle,
+    selections modulo the 3-D conjugate mirror, guided replay)."""
+    t0, x, y, c = (int(v) for v in blk)
+    k = cls[c]
+    F, Ft, b, I = k["fft"], 4, k["block"], k["iters"]
+    kk = dict(k, fft_t=Ft)
+    s, w, toff, off = oimage.area_inputs3(video, mask, t0, x, y, b, k["border"], F, Ft, k["frames"], k["rho"])
+    out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False, max_delta=0.0, widened=False)
+    free = oracle.cfse3(s, w, k["gamma"], I)
+    gsel = np.asarray(gpu_sel[:I], dtype=np.int64)
+    if I:
+        same = gsel == free.sel
+        mir = gsel == mirror3(free.sel, Ft, F)
+        if mir.all() and not same.all():
+            out["mirror"] = True
+        elif not same.all():
+            a = int(np.argmin(same))
+            bq = int(np.argmin(mir)) if not mir.all() else I
+            out["first_div"] = max(a, bq)
+    guided = oracle.cfse3(s, w, k["gamma"], I, forced=gsel.astype(np.int32))
+    if I:
+        ratio = guided.e_sel / np.maximum(guided.e_max, 1e-300)
+        ratio[guided.e_max == 0] = 1.0
+        out["worst_ratio"] = float(ratio.min())
+        e32 = np.asarray(gpu_energy[:I], dtype=np.float64)
+        delta = np.abs(e32 - guided.e_sel) / np.maximum(guided.e_sel, 1e-300)
+        delta[guided.e_sel == 0] = 0.0
+        out["max_delta"] = float(delta.max())
+        if np.any(1.0 - ratio > EPS_TIE + ROUND_K * delta) or out["max_delta"] > DELTA_MAX:
+            out["ok"] = False
+        out["widened"] = bool(np.any(1.0 - ratio > EPS_TIE))
+    tc = toff + (k["frames"] - 1) // 2
+    r0 = off + k["border"]
+    gp = guided.g.real[tc, r0:r0 + b, r0:r0 + b]
+    out["max_pix"] = float(np.max(np.abs(gp - gpu_patch)))
+    if out["max_pix"] > PIX_TOL:
+        out["ok"] = False
+    return out
+
+
 def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None, ests=None, iters=None):
     """Check every block of a batch; patches is the flat patch array (caller
     order), sels / energies the [n, stride] trace or None, ests the per-block

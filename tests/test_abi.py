@@ -54,7 +54,8 @@ int main(void) {
 @pytest.mark.parametrize("bad,status", [
     (dict(fft=48), 1), (dict(fft=128), 2), (dict(block=40), 1), (dict(border=0), 1),
     (dict(border=30), 1), (dict(rho=0.0), 1), (dict(rho=1.5), 1), (dict(gamma=0.0), 1),
-    (dict(gamma=2.0), 1), (dict(iters=-1), 1), (dict(iters=5000), 1)])
+    (dict(gamma=2.0), 1), (dict(iters=-1), 1), (dict(iters=5000), 1), (dict(frames=2), 1),
+    (dict(frames=5), 2), (dict(frames=3), 2)])
 def test_config_validation_statuses(bad, status):
     cls = dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=10)
     cls.update(bad)
