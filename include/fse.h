@@ -59,6 +59,16 @@ typedef enum {
 
 /* fse_config.flags */
 #define FSE_FLAG_TRACE 1u /* record every selection (see fse_get_trace) */
+/* Ordered concealment (no counterpart in the paper, which conceals every block
+ * from the original support): blocks are concealed in the caller's order and
+ * the samples of blocks concealed before a block, where they fall in its
+ * area, join its support at their concealed values with weight
+ * reuse_weight x Eq. (3).  One image class of fft 32 or 64, zero
+ * initialisation, the `out`
+ * image of fse_extrapolate_batch required (the concealed values are read
+ * from it); not with the host-buffer or allocation-free entry points.  On
+ * the GPU a block waits (bounded, 1 s) for the blocks it reuses. */
+#define FSE_FLAG_ORDERED 2u
 
 /*
  * One block-size class.
@@ -105,6 +115,7 @@ typedef struct {
     int init_iters;
     int device;
     unsigned flags;
+    float reuse_weight;   /* FSE_FLAG_ORDERED: weight factor of reused samples, (0, 1] */
 } fse_config;
 
 /* A lost block: image index, top-left sample (x = column, y = row) of B, and

@@ -159,3 +159,54 @@ def conceal_block3(video, mask, t0, x, y, cls, forced=None):
     res = cfse3(s, w, cls["gamma"], cls["iters"], forced=forced)
     tc = toff + (T - 1) // 2
     return res.g.real[tc, off + d:off + d + b, off + d:off + d + b], res
+
+
+# ----------------------------------------------------------- ordered concealment
+def area_inputs_ordered(work, mask, reused, x, y, b, d, F, rho, beta):
+    """Grid inputs when already-concealed samples count as support: `work`
+    holds the original samples and the values concealed so far, `reused`
+    marks the samples concealed so far (lost samples of earlier blocks).
+    Support: inside the image and either not lost (weight w of Eq. (3)) or
+    reused (weight beta w); the block's own B is excluded."""
+    H, W = work.shape
+    M = b + 2 * d
+    off = (F - M) // 2
+    ys = np.arange(y - d, y - d + M)
+    xs = np.arange(x - d, x - d + M)
+    inside = ((ys >= 0) & (ys < H))[:, None] & ((xs >= 0) & (xs < W))[None, :]
+    yc = np.clip(ys, 0, H - 1)
+    xc = np.clip(xs, 0, W - 1)
+    s_area = work[np.ix_(yc, xc)].astype(np.float64)
+    lost = mask[np.ix_(yc, xc)] != 0
+    re = reused[np.ix_(yc, xc)]
+    own_b = np.zeros((M, M), dtype=bool)
+    own_b[d:d + b, d:d + b] = True
+    support = inside & ~own_b & (~lost | re)
+    w_area = weight(M, M, rho, support.astype(np.uint8)) * np.where(lost & re, beta, 1.0)
+    s_grid = np.zeros((F, F))
+    w_grid = np.zeros((F, F))
+    s_grid[off:off + M, off:off + M] = np.where(support, s_area, 0.0)
+    w_grid[off:off + M, off:off + M] = w_area
+    return s_grid, w_grid, off
+
+
+def conceal_ordered(images, mask, blocks, cls, beta, forced=None):
+    """Blocks concealed one after another in the given order; each block's
+    support also holds the samples of the blocks concealed before it (their
+    concealed values, weight beta times Eq. (3)).  One class.  forced: None or
+    per-block selection sequences for a guided replay.  Returns the list of
+    (patch, CfseResult) and the working images."""
+    work = np.asarray(images, dtype=np.float64).copy()
+    reused = np.zeros(work.shape, dtype=bool)
+    b, d, F = cls["block"], cls["border"], cls["fft"]
+    out = []
+    for j, (im, x, y, _c) in enumerate(np.asarray(blocks).reshape(-1, 4)):
+        im, x, y = int(im), int(x), int(y)
+        s, w, off = area_inputs_ordered(work[im], mask[im], reused[im], x, y, b, d, F, cls["rho"], beta)
+        res = cfse(s, w, cls["gamma"], cls["iters"], forced=None if forced is None else forced[j])
+        r0 = off + d
+        patch = res.g.real[r0:r0 + b, r0:r0 + b].copy()
+        work[im, y:y + b, x:x + b] = patch
+        reused[im, y:y + b, x:x + b] = True
+        out.append((patch, res))
+    return out, work

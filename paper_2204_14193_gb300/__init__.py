@@ -25,6 +25,7 @@ FSE_MAX_CLASSES = 4
 FSE_DTYPE_U8, FSE_DTYPE_F32 = 0, 1
 FSE_INIT_ZERO, FSE_INIT_LEARNED = 0, 1
 FSE_FLAG_TRACE = 1
+FSE_FLAG_ORDERED = 2
 STATUS = {0: "FSE_OK", 1: "FSE_ERR_INVALID_ARG", 2: "FSE_ERR_UNSUPPORTED", 3: "FSE_ERR_CUDA",
           4: "FSE_ERR_OOM", 5: "FSE_ERR_TIMEOUT", 6: "FSE_ERR_NOT_TRAINED"}
 
@@ -38,7 +39,7 @@ class fse_class(ctypes.Structure):
 class fse_config(ctypes.Structure):
     _fields_ = [("n_classes", ctypes.c_int), ("cls", fse_class * FSE_MAX_CLASSES),
                 ("init", ctypes.c_int), ("init_iters", ctypes.c_int), ("device", ctypes.c_int),
-                ("flags", ctypes.c_uint)]
+                ("flags", ctypes.c_uint), ("reuse_weight", ctypes.c_float)]
 
 
 class fse_block(ctypes.Structure):
@@ -321,7 +322,7 @@ def he_init(seed: int) -> np.ndarray:
 
 # --------------------------------------------------------- convenience API
 def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero",
-                init_iters: int = 0) -> fse_config:
+                init_iters: int = 0, ordered: bool = False, reuse_weight: float = 0.5) -> fse_config:
     cfg = fse_config()
     cfg.n_classes = len(classes)
     for i, c in enumerate(classes):
@@ -330,7 +331,8 @@ def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero
     cfg.init = FSE_INIT_LEARNED if init == "learned" else FSE_INIT_ZERO
     cfg.init_iters = int(init_iters)
     cfg.device = device
-    cfg.flags = FSE_FLAG_TRACE if trace else 0
+    cfg.flags = (FSE_FLAG_TRACE if trace else 0) | (FSE_FLAG_ORDERED if ordered else 0)
+    cfg.reuse_weight = float(reuse_weight)
     return cfg
 
 
@@ -341,9 +343,9 @@ class Engine:
     """
 
     def __init__(self, classes, device: int = 0, trace: bool = False, init: str = "zero", init_iters: int = 0,
-                 weights=None):
+                 weights=None, ordered: bool = False, reuse_weight: float = 0.5):
         self.classes = [dict(c) for c in classes]
-        self.h = fse_create(make_config(classes, device, trace, init, init_iters))
+        self.h = fse_create(make_config(classes, device, trace, init, init_iters, ordered, reuse_weight))
         self.last_n = 0
         if weights is not None:
             fse_load_init_weights(self.h, weights)

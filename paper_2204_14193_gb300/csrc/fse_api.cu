@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "fse.h"
@@ -126,6 +127,10 @@ struct fse_handle {
     uint8_t *d_tc_w = nullptr;      // tensor-core network: packed B operands
     bool tc_net = false;            // 16x16 blocks with a 16-sample border: tcgen05 kernel
     int *d_err = nullptr;           // device-side error status (bounded waits)
+    // ordered concealment (FSE_FLAG_ORDERED): neighbour lists and done flags
+    int *d_nb_start = nullptr, *d_nb_list = nullptr, *d_done = nullptr;
+    size_t nb_start_cap = 0, nb_list_cap = 0, done_cap = 0;
+    int ordered_n = 0;
     std::string err = "no error";
 };
 
@@ -192,7 +197,17 @@ fse_status validate_config(const fse_config *cfg) {
         if (cfg->init_iters < 0 || cfg->init_iters > 4096)
             return fail(nullptr, FSE_ERR_INVALID_ARG, "init_iters %d not in [0, 4096]", cfg->init_iters);
     }
-    if (cfg->flags & ~FSE_FLAG_TRACE) return fail(nullptr, FSE_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    if (cfg->flags & ~(FSE_FLAG_TRACE | FSE_FLAG_ORDERED))
+        return fail(nullptr, FSE_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    if (cfg->flags & FSE_FLAG_ORDERED) {
+        // fft 16 is excluded: its blocks share warps, and a lane waiting for an
+        // earlier block of its own warp would stall that warp's synchronisation
+        if (cfg->n_classes != 1 || cfg->init != FSE_INIT_ZERO || cfg->cls[0].frames > 1 || cfg->cls[0].fft < 32)
+            return fail(nullptr, FSE_ERR_UNSUPPORTED,
+                        "ordered concealment: one image class of fft 32 or 64 with the zero initialisation");
+        if (!(cfg->reuse_weight > 0.f && cfg->reuse_weight <= 1.f))
+            return fail(nullptr, FSE_ERR_INVALID_ARG, "reuse_weight %g not in (0, 1]", (double)cfg->reuse_weight);
+    }
     return FSE_OK;
 }
 
@@ -418,6 +433,7 @@ fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) 
                 h->d_cnn_out, h->d_blocks, first, cnt, M, C.d, C.b, h->d_est, (long long)MM);
         }
     }
+    if (h->params.ordered) cudaMemsetAsync(h->d_done, 0, (size_t)h->ordered_n * sizeof(int), h->cap_stream);
     cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
     if (nt == 256)
         fse::fse_batch_kernel<256><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params);
@@ -486,10 +502,50 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
     return FSE_OK;
 }
 
+// Ordered concealment: for every block j (caller order), the earlier blocks
+// i < j of the same image whose b x b block meets j's area
+// [x - d, x + b + d) x [y - d, y + b + d): CSR lists, found through a grid of
+// b x b cells.
+void ordered_neighbours(const fse_block *blocks, int n, int b, int d, std::vector<int> &start,
+                        std::vector<int> &list) {
+    auto cell = [](int im, int cy, int cx) {
+        return ((uint64_t)(uint32_t)im << 42) ^ ((uint64_t)(uint32_t)(cy + (1 << 20)) << 21) ^
+               (uint64_t)(uint32_t)(cx + (1 << 20));
+    };
+    auto fdiv = [](int a, int q) { return a >= 0 ? a / q : -((-a + q - 1) / q); };
+    std::unordered_map<uint64_t, std::vector<int>> grid;
+    grid.reserve((size_t)n * 2);
+    start.assign(n + 1, 0);
+    list.clear();
+    for (int j = 0; j < n; ++j) {
+        const fse_block &bj = blocks[j];
+        const int ax0 = bj.x - d, ax1 = bj.x + b + d, ay0 = bj.y - d, ay1 = bj.y + b + d;
+        std::vector<int> cand;
+        for (int cy = fdiv(ay0, b); cy <= fdiv(ay1 - 1, b); ++cy)
+            for (int cx = fdiv(ax0, b); cx <= fdiv(ax1 - 1, b); ++cx) {
+                auto it = grid.find(cell(bj.image, cy, cx));
+                if (it == grid.end()) continue;
+                for (int i : it->second) {
+                    const fse_block &bi = blocks[i];
+                    if (bi.x < ax1 && bi.x + b > ax0 && bi.y < ay1 && bi.y + b > ay0) cand.push_back(i);
+                }
+            }
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        list.insert(list.end(), cand.begin(), cand.end());
+        start[j + 1] = (int)list.size();
+        for (int cy = fdiv(bj.y, b); cy <= fdiv(bj.y + b - 1, b); ++cy)
+            for (int cx = fdiv(bj.x, b); cx <= fdiv(bj.x + b - 1, b); ++cx) grid[cell(bj.image, cy, cx)].push_back(j);
+    }
+}
+
 fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
                      size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks, float *out,
                      float *patches, cudaStream_t stream, const float *est = nullptr, long long est_stride = 0) {
     const bool learned = h->cfg.init == FSE_INIT_LEARNED && est == nullptr;
+    const bool ordered = (h->cfg.flags & FSE_FLAG_ORDERED) != 0;
+    if (ordered && n_blocks > 0 && (!out || est))
+        return fail(h, FSE_ERR_INVALID_ARG, "ordered concealment needs the out image (and no warm start)");
     if (learned && n_blocks > 0 && !h->weights_loaded)
         return fail(h, FSE_ERR_NOT_TRAINED, "learned initialisation: no weights loaded (fse_load_init_weights)");
     if (n_blocks < 0) return fail(h, FSE_ERR_INVALID_ARG, "n_blocks %d < 0", n_blocks);
@@ -624,6 +680,28 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     } else {
         P.est = est;
         P.est_stride = est_stride;
+    }
+    P.err = h->d_err;
+    P.ordered = ordered ? 1 : 0;
+    if (ordered) {
+        std::vector<int> nb_start, nb_list;
+        ordered_neighbours(blocks, n_blocks, h->cfg.cls[0].block, h->cfg.cls[0].border, nb_start, nb_list);
+        for (int i = 0; i < n_blocks; ++i)   // one class: the queue is the caller's order
+            if (pl.sorted[i].orig != i) return fail(h, FSE_ERR_INVALID_ARG, "ordered concealment: queue order");
+        st = grow(h, &h->d_nb_start, &h->nb_start_cap, nb_start.size());
+        if (st != FSE_OK) return st;
+        st = grow(h, &h->d_nb_list, &h->nb_list_cap, std::max<size_t>(nb_list.size(), 1));
+        if (st != FSE_OK) return st;
+        st = grow(h, &h->d_done, &h->done_cap, (size_t)n_blocks);
+        if (st != FSE_OK) return st;
+        FSE_CUDA(h, cudaMemcpy(h->d_nb_start, nb_start.data(), nb_start.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!nb_list.empty())
+            FSE_CUDA(h, cudaMemcpy(h->d_nb_list, nb_list.data(), nb_list.size() * sizeof(int), cudaMemcpyHostToDevice));
+        P.beta = h->cfg.reuse_weight;
+        P.nb_start = h->d_nb_start;
+        P.nb_list = h->d_nb_list;
+        P.done = h->d_done;
+        h->ordered_n = n_blocks;
     }
     int nt = 256, cps = h->max_ctas_per_sm_256;
     st = autotune(h, pl, stream, &nt, &cps);
@@ -886,6 +964,9 @@ void fse_destroy(fse_handle *h) {
         cudaFree(h->d_cnn_x);
         cudaFree(h->d_tc_w);
         cudaFree(h->d_err);
+        cudaFree(h->d_nb_start);
+        cudaFree(h->d_nb_list);
+        cudaFree(h->d_done);
         cudaFree(h->d_cnn_a0);
         cudaFree(h->d_cnn_a1);
         cudaFree(h->d_cnn_out);

@@ -70,7 +70,28 @@ struct DevParams {
     const float2 *tw;                 // 64 entries (cos, sin)(2 pi t / 64)
     const float *est;                 // warm start: per-block estimate (sample units) or nullptr
     long long est_stride;             // floats between two blocks' estimates (block order: orig)
+    // ordered concealment: blocks (caller order = queue order) reuse the
+    // concealed samples of the earlier blocks listed for them
+    int ordered;
+    float beta;                       // weight factor of reused samples
+    const int *nb_start, *nb_list;    // CSR: earlier blocks whose B meets the block's area
+    int *done;                        // per block: concealed output visible (zeroed per launch)
+    int *err;                         // device status word (a bounded wait expired: 5)
 };
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint64_t pk(float lo, float hi) {
@@ -439,6 +460,25 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     float2 *Z = reinterpret_cast<float2 *>(region);
 
     const int b = C.b, d = C.d, M = C.M, off = C.off;
+    const bool ordered = FT == 1 && P.ordered;
+    int nb0 = 0, nb1 = 0;
+    if (ordered) {
+        // the blocks this one reuses must have written their output (bounded)
+        nb0 = P.nb_start[blk.orig];
+        nb1 = P.nb_start[blk.orig + 1];
+        if (lt == 0) {
+            const uint64_t t0 = globaltimer_ns();
+            for (int q = nb0; q < nb1; ++q)
+                while (ld_acquire_gpu(&P.done[P.nb_list[q]]) == 0) {
+                    if (globaltimer_ns() - t0 > 1000000000ull) {
+                        atomicExch(P.err, 5);
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+        }
+        gsync<F, PAIRS, NT, FT>(gr);
+    }
     // ---- S0/S1: gather the area, Eq. (3) weights, z = (w s, w) ----
     // All loads of the thread's grid positions are issued first (clamped to
     // the image, so always in bounds), then the weights are applied: one
@@ -471,10 +511,20 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         const int tau = pl - C.toff;                       // frame of the volume (FT = 1: 0)
         const int fr = blk.image + tau - C.tc;
         const bool own = tau == C.tc && am >= d && am < d + b && an >= d && an < d + b;
-        const bool inA = am >= 0 && am < M && an >= 0 && an < M && !own &&
-                         yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0 &&
-                         (FT == 1 || (tau >= 0 && tau < C.T && fr >= 0 && fr < P.n_images));
-        const float w = inA ? __ldg(&C.wtab[(FT == 1 ? 0 : tau * M * M) + am * M + an]) : 0.f;
+        const bool inV = am >= 0 && am < M && an >= 0 && an < M && !own && yy >= 0 && yy < P.H && xx >= 0 &&
+                         xx < P.W && (FT == 1 || (tau >= 0 && tau < C.T && fr >= 0 && fr < P.n_images));
+        // ordered: a lost sample of an earlier block is reused at its concealed value
+        bool reuse = false;
+        if (ordered && inV && mk[t] != 0) {
+            for (int q = nb0; q < nb1 && !reuse; ++q) {
+                const BlockRec nbk = P.blocks[P.nb_list[q]];
+                reuse = yy >= nbk.y && yy < nbk.y + b && xx >= nbk.x && xx < nbk.x + b;
+            }
+        }
+        const bool inA = inV && (mk[t] == 0 || reuse);
+        const float w = inA ? __ldg(&C.wtab[(FT == 1 ? 0 : tau * M * M) + am * M + an]) * (reuse ? P.beta : 1.f)
+                            : 0.f;
+        if (reuse) sv[t] = __ldcg(&P.out[((size_t)blk.image * P.H + yy) * P.W + xx]);
         // warm start: the support holds the residual of the estimate
         const float sr = (inA && P.est != nullptr) ? sv[t] - P.est[blk.orig * P.est_stride + am * M + an] : sv[t];
         const float ws = w * sr;
@@ -672,6 +722,11 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
             if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
         }
+    }
+    if (ordered) {   // publish: every thread's output stores, then the flag
+        __threadfence();
+        gsync<F, PAIRS, NT, FT>(gr);
+        if (lt == 0) st_release_gpu(&P.done[blk.orig], 1);
     }
 }
 

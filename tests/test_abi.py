@@ -77,3 +77,16 @@ def test_learned_config_validation(n_classes, init_iters, status):
     with pytest.raises(P.FseError) as ei:
         P.fse_create(P.make_config([cls] * n_classes, init="learned", init_iters=init_iters))
     assert ei.value.status == status
+
+
+@pytest.mark.parametrize("kw,status", [(dict(ordered=True, reuse_weight=0.0), 1), (dict(ordered=True, reuse_weight=1.5), 1),
+                                       (dict(ordered=True, n=2), 2), (dict(ordered=True, init="learned"), 2),
+                                       (dict(ordered=True, fft=16), 2)])
+def test_ordered_config_validation(kw, status):
+    cls = dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=10)
+    n = kw.pop("n", 1)
+    if "fft" in kw:
+        cls = dict(block=4, border=6, fft=kw.pop("fft"), rho=0.8, gamma=0.5, iters=10)
+    with pytest.raises(P.FseError) as ei:
+        P.fse_create(P.make_config([cls] * n, **kw))
+    assert ei.value.status == status
