@@ -5,10 +5,11 @@ CPU-baseline leg of ``bench.py`` are the only callers.  The product library
 never imports this package, and this package never imports the product.
 
 The numerical kernels live in plain C (``fse_oracle.c``, ``cnn_oracle.c``,
-``fse3_oracle.c`` for video volumes),
-compiled with gcc into ``liboracle.so`` beside them; this module wraps them
-with numpy arrays.  ``image`` holds the image-level driver (gather of the
-extrapolation area, Eq. (3) weighting, fill of the loss area).
+``fse3_oracle.c`` for video volumes), compiled with gcc into
+``liboracle.so`` beside them; this module wraps them with numpy arrays.
+``image`` holds the image-level driver (gather of the extrapolation area,
+Eq. (3) weighting, fill of the loss area; warm start, video volumes and
+ordered concealment), ``cnn`` the learned-initialisation network.
 """
 from __future__ import annotations
 

@@ -8,7 +8,9 @@ marked lost in the mask (any block) or belong to the block's own B are not
 support: their weight is 0.
 Eq. (3) then gives w on A, Algorithm 1 (``oracle.cfse``) the model g, and
 Re{g} replaces the samples of B (the last loop of Algorithm 1).  Blocks are
-concealed independently of each other from the original mask.
+concealed independently of each other from the original mask, except in
+``conceal_ordered`` (earlier blocks' concealed samples reused as support).
+``area_inputs3`` / ``conceal_block3`` build and conceal video volumes.
 """
 from __future__ import annotations
 

@@ -9,6 +9,11 @@
 //   I iterations               -> argmax |R_w|^2, c = gamma R_w[u,v] / W[0,0],
 //                                 R_w[k,l] -= c W[k-u, l-v] (circular)
 //   Re{g} on B                 -> g = sum c phi_(u,v), accumulated per selection
+// Video volumes (class frames = 3) run the same steps on a 4 x F x F grid
+// (the block's frame and its neighbours; a temporal pass completes the
+// transform, shifts are circular in all three dimensions).  Ordered
+// concealment lets a block wait for the earlier blocks in its area and reuse
+// their concealed samples.
 //
 // Layout of one block's spectrum (F x F bins, k = row, l = column):
 //   thread t of the block owns column c = t % (F/2) and its partner column
