@@ -131,6 +131,7 @@ struct fse_handle {
     int *d_nb_start = nullptr, *d_nb_list = nullptr, *d_done = nullptr;
     size_t nb_start_cap = 0, nb_list_cap = 0, done_cap = 0;
     int ordered_n = 0;
+    bool ext = false;               // video volumes or ordered concealment: the EXT kernel
     std::string err = "no error";
 };
 
@@ -436,9 +437,11 @@ fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) 
     if (h->params.ordered) cudaMemsetAsync(h->d_done, 0, (size_t)h->ordered_n * sizeof(int), h->cap_stream);
     cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
     if (nt == 256)
-        fse::fse_batch_kernel<256><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params);
+        h->ext ? fse::fse_batch_kernel<256, true><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params)
+               : fse::fse_batch_kernel<256, false><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params);
     else
-        fse::fse_batch_kernel<128><<<grid, 128, h->smem_bytes, h->cap_stream>>>(h->params);
+        h->ext ? fse::fse_batch_kernel<128, true><<<grid, 128, h->smem_bytes, h->cap_stream>>>(h->params)
+               : fse::fse_batch_kernel<128, false><<<grid, 128, h->smem_bytes, h->cap_stream>>>(h->params);
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -754,13 +757,24 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
         smem = std::max(smem, (size_t)fse::cta_region_bytes(F));
     }
     h->smem_bytes = smem;
+    h->ext = (cfg->flags & FSE_FLAG_ORDERED) != 0;
+    for (int c = 0; c < cfg->n_classes; ++c) h->ext = h->ext || cfg->cls[c].frames > 1;
+    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
     CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int occ = 0, occ2 = 0;
-    CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, smem));
-    CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fse::fse_batch_kernel<256>, 256, smem));
+    if (h->ext) {
+        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128, true>, 128, smem));
+        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fse::fse_batch_kernel<256, true>, 256, smem));
+    } else {
+        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, smem));
+        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fse::fse_batch_kernel<256>, 256, smem));
+    }
     if (occ < 1 || occ2 < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
     h->max_ctas_per_sm = occ;
     h->max_ctas_per_sm_256 = occ2;

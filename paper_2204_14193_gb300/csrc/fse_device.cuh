@@ -265,8 +265,11 @@ __device__ __forceinline__ void fft_pass(float2 *Z, const float2 *s_tw, const Gr
     constexpr int N1 = NL * R2 / TB;      // step-1 tasks per thread
     constexpr int N2 = NL * R1 / TB;      // step-2 tasks per thread
     static_assert(N1 * TB == NL * R2 && N2 * TB == NL * R1, "FFT tasks must tile the group");
-    // line L of plane L / F: offset (L / F) F FP + (L % F) LS
-    auto lbase = [](int L) { return (L / F) * F * FP + (L % F) * LS; };
+    // line L of plane L / F: offset (L / F) F FP + (L % F) LS (images: L LS)
+    auto lbase = [](int L) {
+        if constexpr (FT == 1) return L * LS;
+        else return (L / F) * F * FP + (L % F) * LS;
+    };
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
         const int t = gr.lt + j * TB;
@@ -443,13 +446,292 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 
 // ------------------------------------------------------- per-block worker
 // NP: B samples per thread (compile time; the caller picks the smallest
-// variant that covers b*b).  FT: temporal transform size (1: an image area;
-// 4: a video volume of C.T frames centred on the block's frame, transform
-// grid FT x F x F with bins indexed (t F + k) F + l -- the same Algorithm 1
-// with 3-D basis functions and 3-D circular shifts).
-template <int F, int PAIRS, int NT, int NP, int FT = 1>
+// variant that covers b*b).  EXT: built with ordered concealment.
+template <int F, int PAIRS, int NT, int NP, bool EXT = false>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
+    using G = Geo<F, PAIRS>;
+    constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
+    Grp gr;
+    gr.g = threadIdx.x / TB;
+    gr.lt = threadIdx.x % TB;
+    const bool active = gr.g < count;
+    gr.amask = __ballot_sync(0xffffffffu, active);
+    if (!active) return;
+    const int lt = gr.lt;
+
+    const BlockRec blk = P.blocks[first + gr.g];
+    unsigned char *region = smem + gr.g * G::REGION;
+    float2 *Z = reinterpret_cast<float2 *>(region);
+
+    const int b = C.b, d = C.d, M = C.M, off = C.off;
+    // ordered concealment (EXT builds only): the blocks this one reuses must
+    // have written their output (bounded wait)
+    int nb0 = 0, nb1 = 0;
+    if constexpr (EXT) {
+        if (P.ordered) {
+            nb0 = P.nb_start[blk.orig];
+            nb1 = P.nb_start[blk.orig + 1];
+            if (lt == 0) {
+                const uint64_t t0 = globaltimer_ns();
+                for (int q = nb0; q < nb1; ++q)
+                    while (ld_acquire_gpu(&P.done[P.nb_list[q]]) == 0) {
+                        if (globaltimer_ns() - t0 > 1000000000ull) {
+                            atomicExch(P.err, 5);
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+            }
+            gsync<F, PAIRS, NT>(gr);
+        }
+    }
+    // ---- S0/S1: gather the area, Eq. (3) weights, z = (w s, w) ----
+    // All loads of the thread's grid positions are issued first (clamped to
+    // the image, so always in bounds), then the weights are applied: one
+    // memory round trip instead of one per position.
+    constexpr int NPOS = F * F / TB;
+    float sv[NPOS];
+    uint8_t mk[NPOS];
+#pragma unroll
+    for (int t = 0; t < NPOS; ++t) {
+        const int pix = lt + t * TB;
+        const int yy = min(max(blk.y - d + pix / F - off, 0), P.H - 1);
+        const int xx = min(max(blk.x - d + pix % F - off, 0), P.W - 1);
+        mk[t] = P.mask[((size_t)blk.image * P.H + yy) * P.W + xx];
+        const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+        sv[t] = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
+                             : reinterpret_cast<const float *>(row)[xx];
+    }
+    float smax = 0.f;
+#pragma unroll
+    for (int t = 0; t < NPOS; ++t) {
+        const int pix = lt + t * TB;
+        const int m = pix / F, n = pix % F;
+        const int am = m - off, an = n - off;
+        const int yy = blk.y - d + am, xx = blk.x - d + an;
+        bool inA = am >= 0 && am < M && an >= 0 && an < M &&
+                   !(am >= d && am < d + b && an >= d && an < d + b) &&
+                   yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0;
+        float wscale = 1.f;
+        if constexpr (EXT) {
+            // ordered: a lost sample of an earlier block is reused at its concealed value
+            if (P.ordered && !inA && am >= 0 && am < M && an >= 0 && an < M &&
+                !(am >= d && am < d + b && an >= d && an < d + b) && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W) {
+                bool reuse = false;
+                for (int q = nb0; q < nb1 && !reuse; ++q) {
+                    const BlockRec nbk = P.blocks[P.nb_list[q]];
+                    reuse = yy >= nbk.y && yy < nbk.y + b && xx >= nbk.x && xx < nbk.x + b;
+                }
+                if (reuse) {
+                    inA = true;
+                    wscale = P.beta;
+                    sv[t] = __ldcg(&P.out[((size_t)blk.image * P.H + yy) * P.W + xx]);
+                }
+            }
+        }
+        float w = inA ? __ldg(&C.wtab[am * M + an]) : 0.f;
+        if constexpr (EXT) w *= wscale;
+        // warm start: the support holds the residual of the estimate
+        const float sr = (inA && P.est != nullptr) ? sv[t] - P.est[blk.orig * P.est_stride + am * M + an] : sv[t];
+        const float ws = w * sr;
+        if (inA) smax = fmaxf(smax, fabsf(sr));
+        Z[m * FP + n] = make_float2(ws, w);
+    }
+    // alpha = the power of two in (max|s| / 2, max|s|] over the support:
+    // balances the two real signals packed into one complex FFT (an exact
+    // scaling; a maximum, so it is independent of the thread mapping)
+    const float tmaxs = group_max<F, PAIRS, NT>(smax, gr, rsh);
+    float alpha = 1.f;
+    if (tmaxs > 0.f) {
+        int e;
+        frexpf(tmaxs, &e);
+        alpha = ldexpf(1.f, e - 1);
+    }
+    for (int pix = lt; pix < F * F; pix += TB) {
+        const int m = pix / F, n = pix % F;
+        Z[m * FP + n].y *= alpha;
+    }
+    gsync<F, PAIRS, NT>(gr);
+    // ---- S2/S3: FFT2 of z ----
+    fft_pass<F, PAIRS, NT, true>(Z, s_tw, gr);
+    fft_pass<F, PAIRS, NT, false>(Z, s_tw, gr);
+
+    // ---- split into R_w = FFT{w s} and W = FFT{w} ----
+    // W chunk rows k >= F/2 + 1 lie beyond the padded FFT buffer, so they are
+    // written at once; the others are held until every thread has read Z.
+    const int c0 = lt % LPR, r0 = lt / LPR;
+    const float ainv = 1.f / alpha;
+    float4 *Wd = reinterpret_cast<float4 *>(region);
+    constexpr int SAFE = F / 2 + 1;
+    uint64_t Rre[PAIRS], Rim[PAIRS];
+    float4 Wc[PAIRS];
+#pragma unroll
+    for (int i = 0; i < PAIRS; ++i) {
+        const int k = G::row(r0, i), km = (F - k) & (F - 1);
+        float2 R2[2], W2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = c0 + h * (F / 2), lm = (F - l) & (F - 1);
+            const float2 z = Z[k * FP + l], zm = Z[km * FP + lm];
+            R2[h] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+            W2[h] = make_float2(0.5f * ainv * (z.y + zm.y), 0.5f * ainv * (zm.x - z.x));
+        }
+        Rre[i] = pk(R2[0].x, R2[1].x);
+        Rim[i] = pk(R2[0].y, R2[1].y);
+        Wc[i] = make_float4(W2[0].x, W2[1].x, W2[0].y, W2[1].y);
+        if (k >= SAFE) {
+            Wd[k * F + c0] = Wc[i];
+            Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        }
+    }
+    const float W00 = Z[0].y * ainv;
+    gsync<F, PAIRS, NT>(gr);
+#pragma unroll
+    for (int i = 0; i < PAIRS; ++i) {
+        const int k = G::row(r0, i);
+        if (k < SAFE) {
+            Wd[k * F + c0] = Wc[i];
+            Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        }
+        if (G::RUNS && k < G::WROWS - F) {   // the copy of the first rows after row F-1
+            Wd[(k + F) * F + c0] = Wc[i];
+            Wd[(k + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        }
+    }
+    gsync<F, PAIRS, NT>(gr);
+
+    // ---- B samples owned by this thread (NP of them; samples j >= b*b are
+    //      computed but never stored) ----
+    int pm_[NP], pn_[NP];
+    float acc[NP];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+        const int j = lt + t * TB;
+        pm_[t] = off + d + j / b;
+        pn_[t] = off + d + j % b;
+        acc[t] = 0.f;
+    }
+    const float W0bar = W00 > 0.f ? 1.f / W00 : 0.f;
+    const float cg = C.gamma * W0bar;
+
+    // ---- S5: first selection (energies of R_w^(0)) ----
+    float q[NQ];
+    float tmax = 0.f;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const uint64_t e0 = energy2(Rre[4 * j], Rim[4 * j]), e1 = energy2(Rre[4 * j + 1], Rim[4 * j + 1]);
+        const uint64_t e2 = energy2(Rre[4 * j + 2], Rim[4 * j + 2]), e3 = energy2(Rre[4 * j + 3], Rim[4 * j + 3]);
+        const float a = max3f(lo_of(e0), hi_of(e0), lo_of(e1));
+        const float bq = max3f(hi_of(e1), lo_of(e2), hi_of(e2));
+        q[j] = max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3)));
+        tmax = fmaxf(tmax, q[j]);
+    }
+    const int iters = C.iters;
+    Pick pick;
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, 0);
+
+    const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
+    for (int nu = 1; nu <= iters; ++nu) {
+        // ---- S6/S7: coefficient and model ----
+        const float cr = pick.rr * cg, ci = pick.ri * cg;
+        const int u = (int)(pick.idx / F), v = (int)(pick.idx % F);
+        if (P.tr_sel != nullptr && lt == 0) {
+            const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
+            P.tr_sel[o] = (int)pick.idx;
+            P.tr_energy[o] = __uint_as_float(pick.ebits);
+            P.tr_coef[o] = make_float2(cr, ci);
+        }
+        // model update of this selection, evaluated on B: g += c phi_(u,v)
+        // (independent of the residual update and of the next reduction)
+        auto model = [&]() {
+#pragma unroll
+            for (int t = 0; t < NP; ++t) {
+                const int ph = (u * pm_[t] + v * pn_[t]) & (F - 1);
+                const float2 tw = s_tw[ph * (64 / F)];
+                acc[t] = fmaf(cr, tw.x, fmaf(-ci, tw.y, acc[t]));
+            }
+        };
+        if (nu == iters) {
+            model();
+            break;
+        }
+        // ---- S8: R_w[k,l] -= c W[k-u, l-v] fused with |R_w|^2 and max ----
+        const uint64_t ncr = pk(-cr, -cr), pci = pk(ci, ci), nci = pk(-ci, -ci);
+        // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
+        // at pair iw.  Pairs before the wrap address from A, the others from
+        // A - F*F, so each load needs one select and an immediate offset.
+        // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
+        // contiguous in W (rows F.. repeat rows 0..6): one base per run.
+        const int qcol = (c0 - v) & (F - 1);
+        const int rb = (r0 - u) & (F - 1);
+        const int iw = (F - rb + RSTEP - 1) / RSTEP;
+        const ulonglong2 *A = Wq + rb * F + qcol;
+        const ulonglong2 *A2 = A - F * F;
+        const ulonglong2 *Ar[G::RUNS ? PAIRS / 8 : 1];
+#pragma unroll
+        for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
+            Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+        tmax = 0.f;
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            float ev[8];
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+                const int i = 4 * j + ii;
+                // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
+                const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                                             : (i < iw ? A : A2)[i * RSTEP * F];
+                const uint64_t wre = w.x, wim = w.y;
+                uint64_t a = fma2(ncr, wre, Rre[i]);
+                Rre[i] = fma2(pci, wim, a);
+                uint64_t bb = fma2(ncr, wim, Rim[i]);
+                Rim[i] = fma2(nci, wre, bb);
+                const uint64_t e = energy2(Rre[i], Rim[i]);
+                ev[2 * ii] = lo_of(e);
+                ev[2 * ii + 1] = hi_of(e);
+            }
+            const float a = max3f(ev[0], ev[1], ev[2]);
+            const float bq = max3f(ev[3], ev[4], ev[5]);
+            q[j] = max3f(a, bq, fmaxf(ev[6], ev[7]));
+            tmax = fmaxf(tmax, q[j]);
+        }
+        model();
+        // ---- S5: next selection ----
+        pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, nu & 1);
+    }
+
+    // ---- S10: write Re{g} on B ----
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+        const int j = lt + t * TB;
+        if (j < b * b) {
+            const int pm = j / b, pn = j % b;
+            const float val =
+                acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
+            if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
+            if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
+        }
+    }
+    if constexpr (EXT) {
+        if (P.ordered) {   // publish: every thread's output stores, then the flag
+            __threadfence();
+            gsync<F, PAIRS, NT>(gr);
+            if (lt == 0) st_release_gpu(&P.done[blk.orig], 1);
+        }
+    }
+}
+
+// Video volumes: the same steps for a volume of C.T frames centred on the
+// block's frame, transform grid FT x F x F with bins indexed (t F + k) F + l
+// -- Algorithm 1 with 3-D basis functions and 3-D circular shifts.  (Kept
+// apart from process() so that the image path's code is not touched by the
+// temporal dimension.)
+template <int F, int PAIRS, int NT, int NP, int FT>
+__device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &C, int first, int count,
+                                            unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
+    static_assert(FT > 1, "image areas run process()");
+    constexpr bool EXT = false;   // ordered concealment is for image classes
     using G = Geo<F, PAIRS, FT>;
     constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
     Grp gr;
@@ -465,7 +747,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     float2 *Z = reinterpret_cast<float2 *>(region);
 
     const int b = C.b, d = C.d, M = C.M, off = C.off;
-    const bool ordered = FT == 1 && P.ordered;
+    const bool ordered = EXT && FT == 1 && P.ordered;   // EXT: compiled with ordered concealment
     int nb0 = 0, nb1 = 0;
     if (ordered) {
         // the blocks this one reuses must have written their output (bounded)
@@ -735,27 +1017,29 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     }
 }
 
-template <int F, int PAIRS, int NT, int FT = 1>
+template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false>
 __device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
                                               unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
     constexpr int TB = Geo<F, PAIRS, FT>::TB;
     if constexpr (FT == 1) {
         constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
         constexpr int NPL = PAIRS / 2;                // covers b <= F/2
-        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS>(P, C, first, count, smem, s_tw, rsh);
-        else process<F, PAIRS, NT, NPL>(P, C, first, count, smem, s_tw, rsh);
+        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT>(P, C, first, count, smem, s_tw, rsh);
+        else process<F, PAIRS, NT, NPL, EXT>(P, C, first, count, smem, s_tw, rsh);
     } else {
         // a volume's block group is FT times larger: b <= F/2 needs
         // F^2/4 / TB = PAIRS / (2 FT) samples per thread (at least 1)
         constexpr int NPV = PAIRS / (2 * FT) > 0 ? PAIRS / (2 * FT) : 1;
-        process<F, PAIRS, NT, NPV, FT>(P, C, first, count, smem, s_tw, rsh);
+        process_vol<F, PAIRS, NT, NPV, FT>(P, C, first, count, smem, s_tw, rsh);
     }
 }
 
 // ------------------------------------------------------ persistent kernel
-// NT threads per CTA (128 or 256), 64 KB of dynamic shared memory, at most
-// three CTAs per SM.
-template <int NT>
+// NT threads per CTA (128 or 256), up to 71 KB of dynamic shared memory, at
+// most three CTAs per SM.  EXT: compiled with video volumes and ordered
+// concealment (batches of image classes alone run the variant without them,
+// whose register allocation and code they do not burden).
+template <int NT, bool EXT = false>
 __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant__ DevParams P) {
     constexpr int PAIRS = 2048 / NT;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -775,14 +1059,16 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
         const DevClass &C = P.cls[P.seg_cls[sg]];
         const int first = P.seg_block_start[sg] + (item - item0) * C.bpi;
         const int count = min(C.bpi, P.seg_block_start[sg] + P.seg_block_count[sg] - first);
-        if (C.FT == 4) {
-            if (C.F == 32) process_class<32, PAIRS, NT, 4>(P, C, first, count, smem, s_tw, &rsh);
-            else process_class<16, PAIRS, NT, 4>(P, C, first, count, smem, s_tw, &rsh);
+        if (EXT && C.FT == 4) {
+            if constexpr (EXT) {
+                if (C.F == 32) process_class<32, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh);
+                else process_class<16, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh);
+            }
         } else {
             switch (C.F) {
-                case 64: process_class<64, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
-                case 32: process_class<32, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
-                default: process_class<16, PAIRS, NT>(P, C, first, count, smem, s_tw, &rsh); break;
+                case 64: process_class<64, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
+                case 32: process_class<32, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
+                default: process_class<16, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
             }
         }
         __syncthreads();
