@@ -88,7 +88,8 @@ typedef enum {
  *          Algorithm 1 runs on a 4 x F x F transform grid (the volume in
  *          planes 0..2) with 3-D basis functions and circular shifts.  Volume
  *          classes need fft 16 or 32; they are not available with the learned
- *          initialisation, fse_get_area_model or the allocation-free entry.
+ *          initialisation, the warm start, fse_get_area_model or the
+ *          allocation-free entry.
  */
 typedef struct {
     int block;

@@ -821,6 +821,8 @@ fse_status fse_extrapolate_batch_init(fse_handle *h, const void *images, int dty
                                       size_t est_stride, float *out, float *patches, void *cuda_stream) {
     if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
     if (n_blocks > 0 && !init_estimate) return fail(h, FSE_ERR_INVALID_ARG, "init_estimate is NULL");
+    for (int c = 0; c < h->cfg.n_classes; ++c)
+        if (h->cfg.cls[c].frames > 1) return fail(h, FSE_ERR_UNSUPPORTED, "the warm start is for image classes");
     long long maxMM = 0;
     for (int c = 0; c < h->cfg.n_classes; ++c) {
         const long long M = h->cfg.cls[c].block + 2 * h->cfg.cls[c].border;

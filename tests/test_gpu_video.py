@@ -99,4 +99,12 @@ def test_video_class_rejected_where_unsupported(P):
     with pytest.raises(P.FseError) as ei:
         eng.area_model()
     assert ei.value.status == 2
+    video = torch.zeros((3, 64, 64), dtype=torch.uint8, device="cuda")
+    mask = torch.zeros((3, 64, 64), dtype=torch.uint8, device="cuda")
+    mask[1, 16:24, 16:24] = 1
+    est = torch.zeros((1, 32 * 32), dtype=torch.float32, device="cuda")
+    with pytest.raises(P.FseError) as ei:
+        eng.run_init(video, mask, np.array([[1, 16, 16, 0]], np.int32), est,
+                     patches=torch.zeros(64, dtype=torch.float32, device="cuda"))
+    assert ei.value.status == 2
     eng.close()
