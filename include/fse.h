@@ -194,6 +194,14 @@ fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n);
  * and mask to the handle's device staging buffers, runs the batch, copies the
  * patches (layout as above) back, and synchronises the stream before it
  * returns.  `patches` is a host FP32 array of sum_i b_i^2 values.
+ * With two or more images (zero initialisation, no trace, not ordered) the
+ * call is a pipeline: the block list is cut into up to 3 contiguous chunks
+ * (1/16, 14/16 and 1/16 of a large batch), the images are uploaded in order
+ * on a second stream while the chunks whose images (and, for video volumes,
+ * neighbouring frames) are resident are concealed on `cuda_stream`, and each
+ * chunk's patches are read back on a third stream once its launch ends.
+ * Blocks listed in image order give the most overlap; any order gives the
+ * same patches, bit for bit.
  */
 fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dtype,
                                       int n_images, int height, int width, size_t pitch_bytes,

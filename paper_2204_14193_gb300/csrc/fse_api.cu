@@ -30,6 +30,9 @@ namespace {
 
 thread_local std::string g_create_error = "no error";
 
+// chunks of the pipelined host-buffer path (upload / conceal / read back)
+constexpr int kHostChunks = 3;
+
 struct DeviceGuard {  // restores the caller's current device
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -132,6 +135,17 @@ struct fse_handle {
     size_t nb_start_cap = 0, nb_list_cap = 0, done_cap = 0;
     int ordered_n = 0;
     bool ext = false;               // video volumes or ordered concealment: the EXT kernel
+    // pipelined host-buffer path: upload and read-back streams, per-chunk
+    // events, the chunks' sorted block lists and work-queue heads
+    bool pipe_ready = false;
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in[kHostChunks] = {}, ev_k[kHostChunks] = {};
+    BlockRec *d_cblocks = nullptr;
+    size_t cblocks_cap = 0;
+    BlockRec *h_cblocks = nullptr;  // pinned staging
+    size_t h_cblocks_cap = 0;
+    int *d_ccounter = nullptr;
     std::string err = "no error";
 };
 
@@ -212,7 +226,7 @@ fse_status validate_config(const fse_config *cfg) {
     return FSE_OK;
 }
 
-// Validation of one batch call; fills the sorted plan on success.
+// The sorted plan of one batch call.
 struct Plan {
     std::vector<BlockRec> sorted;
     int n_seg = 0;
@@ -225,8 +239,12 @@ struct Plan {
     uint64_t mix_sig = 0;
 };
 
-fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
-                             size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks, Plan &pl) {
+// Argument checks of one batch call (geometry, every block's class and
+// position); *patch_total = sum of b^2 over the blocks.
+fse_status validate_batch(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
+                          size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks,
+                          long long *patch_total) {
+    *patch_total = 0;
     if (n_blocks < 0) return fail(h, FSE_ERR_INVALID_ARG, "n_blocks %d < 0", n_blocks);
     if (dtype != FSE_DTYPE_U8 && dtype != FSE_DTYPE_F32) return fail(h, FSE_ERR_INVALID_ARG, "dtype %d unknown", dtype);
     if (n_blocks == 0) return FSE_OK;
@@ -238,12 +256,7 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
     if (dtype == FSE_DTYPE_F32 && (pitch % 4 != 0 || (reinterpret_cast<uintptr_t>(images) & 3)))
         return fail(h, FSE_ERR_INVALID_ARG, "FP32 images need 4-byte aligned base and pitch");
     const fse_config &cfg = h->cfg;
-    // class order of the queue: largest F first, then class index
-    int order[FSE_MAX_CLASSES];
-    for (int i = 0; i < cfg.n_classes; ++i) order[i] = i;
-    std::stable_sort(order, order + cfg.n_classes,
-                     [&](int a, int b) { return cfg.cls[a].fft > cfg.cls[b].fft; });
-    std::vector<int> cnt(cfg.n_classes, 0);
+    long long acc = 0;
     for (int i = 0; i < n_blocks; ++i) {
         const fse_block &bk = blocks[i];
         if (bk.cls < 0 || bk.cls >= cfg.n_classes)
@@ -252,8 +265,27 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         if (bk.image < 0 || bk.image >= n_images || bk.x < 0 || bk.y < 0 || bk.x + b > width || bk.y + b > height)
             return fail(h, FSE_ERR_INVALID_ARG, "block %d (image %d, x %d, y %d, b %d) is not inside the image", i,
                         bk.image, bk.x, bk.y, b);
-        cnt[bk.cls]++;
+        acc += (long long)b * b;
     }
+    *patch_total = acc;
+    return FSE_OK;
+}
+
+// Validation and plan of one batch call: blocks bucketed by class (largest F
+// first), work items per class, patch offsets in the caller's order.
+fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
+                             size_t pitch, const uint8_t *mask, const fse_block *blocks, int n_blocks, Plan &pl) {
+    fse_status st = validate_batch(h, images, dtype, n_images, height, width, pitch, mask, blocks, n_blocks,
+                                   &pl.patch_total);
+    if (st != FSE_OK || n_blocks == 0) return st;
+    const fse_config &cfg = h->cfg;
+    // class order of the queue: largest F first, then class index
+    int order[FSE_MAX_CLASSES];
+    for (int i = 0; i < cfg.n_classes; ++i) order[i] = i;
+    std::stable_sort(order, order + cfg.n_classes,
+                     [&](int a, int b) { return cfg.cls[a].fft > cfg.cls[b].fft; });
+    std::vector<int> cnt(cfg.n_classes, 0);
+    for (int i = 0; i < n_blocks; ++i) cnt[blocks[i].cls]++;
     std::vector<long long> poff(n_blocks);
     long long acc = 0;
     for (int i = 0; i < n_blocks; ++i) {
@@ -261,7 +293,6 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         const int b = cfg.cls[blocks[i].cls].block;
         acc += (long long)b * b;
     }
-    pl.patch_total = acc;
     std::vector<int> start(cfg.n_classes, 0);
     int pos = 0, items = 0;
     pl.n_seg = 0;
@@ -302,6 +333,38 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
     }
     pl.mix_sig = sig;
     return FSE_OK;
+}
+
+// Per-class constants of a launch (learned: the iterations after the network).
+void set_classes(const fse_handle *h, DevParams &P, bool learned) {
+    for (int c = 0; c < h->cfg.n_classes; ++c) {
+        const fse_class &k = h->cfg.cls[c];
+        fse::DevClass &D = P.cls[c];
+        D.F = k.fft;
+        D.b = k.block;
+        D.d = k.border;
+        D.M = k.block + 2 * k.border;
+        D.off = (k.fft - D.M) / 2;
+        D.iters = (learned && h->cfg.init_iters > 0) ? h->cfg.init_iters : k.iters;
+        D.FT = k.frames > 1 ? 4 : 1;
+        D.T = k.frames > 1 ? k.frames : 1;
+        D.tc = (D.T - 1) / 2;
+        D.toff = (D.FT - D.T) / 2;
+        D.bpi = 4096 / (k.fft * k.fft * D.FT);
+        D.gamma = k.gamma;
+        D.wtab = h->d_wtab[c];
+    }
+}
+
+// The persistent concealment kernel of a handle: 128 or 256 threads per CTA,
+// the image-only or the extended instantiation.
+void launch_fse(const fse_handle *h, int nt, int grid, const DevParams &P, cudaStream_t s) {
+    if (nt == 256)
+        h->ext ? fse::fse_batch_kernel<256, true><<<grid, 256, h->smem_bytes, s>>>(P)
+               : fse::fse_batch_kernel<256, false><<<grid, 256, h->smem_bytes, s>>>(P);
+    else
+        h->ext ? fse::fse_batch_kernel<128, true><<<grid, 128, h->smem_bytes, s>>>(P)
+               : fse::fse_batch_kernel<128, false><<<grid, 128, h->smem_bytes, s>>>(P);
 }
 
 template <typename T>
@@ -435,13 +498,8 @@ fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) 
         }
     }
     if (h->params.ordered) cudaMemsetAsync(h->d_done, 0, (size_t)h->ordered_n * sizeof(int), h->cap_stream);
-    cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->cap_stream);
-    if (nt == 256)
-        h->ext ? fse::fse_batch_kernel<256, true><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params)
-               : fse::fse_batch_kernel<256, false><<<grid, 256, h->smem_bytes, h->cap_stream>>>(h->params);
-    else
-        h->ext ? fse::fse_batch_kernel<128, true><<<grid, 128, h->smem_bytes, h->cap_stream>>>(h->params)
-               : fse::fse_batch_kernel<128, false><<<grid, 128, h->smem_bytes, h->cap_stream>>>(h->params);
+    cudaMemsetAsync(h->params.counter, 0, sizeof(int), h->cap_stream);
+    launch_fse(h, nt, grid, h->params, h->cap_stream);
     cudaError_t le = cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -638,23 +696,7 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         P.seg_block_count[sg] = pl.seg_block_count[sg];
     }
     P.total_items = pl.total_items;
-    for (int c = 0; c < h->cfg.n_classes; ++c) {
-        const fse_class &k = h->cfg.cls[c];
-        fse::DevClass &D = P.cls[c];
-        D.F = k.fft;
-        D.b = k.block;
-        D.d = k.border;
-        D.M = k.block + 2 * k.border;
-        D.off = (k.fft - D.M) / 2;
-        D.iters = (learned && h->cfg.init_iters > 0) ? h->cfg.init_iters : k.iters;
-        D.FT = k.frames > 1 ? 4 : 1;
-        D.T = k.frames > 1 ? k.frames : 1;
-        D.tc = (D.T - 1) / 2;
-        D.toff = (D.FT - D.T) / 2;
-        D.bpi = 4096 / (k.fft * k.fft * D.FT);
-        D.gamma = k.gamma;
-        D.wtab = h->d_wtab[c];
-    }
+    set_classes(h, P, learned);
     P.n_images = n_images;
     P.counter = h->d_counter;
     P.tr_sel = trace ? h->d_tr_sel : nullptr;
@@ -716,6 +758,162 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     h->graph_valid = true;
     h->plan_key = key;
     FSE_CUDA(h, cudaGraphLaunch(h->gexec, stream));
+    return FSE_OK;
+}
+
+// Host-buffer batches over several images run as a pipeline of up to
+// kHostChunks chunks: the images are uploaded in order on one stream while
+// the chunks already resident are concealed on the caller's stream, and each
+// chunk's patches are read back on a third stream as soon as its launch ends.
+// A chunk is a contiguous range of the caller's block list and needs the
+// images up to the last one its blocks read (the frames +-(T-1)/2 around a
+// video volume's frame), so with blocks listed in image order the first
+// launch starts after 1/16 of the upload and only 1/16 of the patches are
+// read back after the last launch; in any other order the pipeline is still
+// correct, with less overlap.  Every block
+// is concealed by the same code from the same inputs as in the one-launch
+// path, so the patches are identical bit for bit.  The caller has validated
+// the batch (image, class and position of every block).
+fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_images, int height, int width,
+                            size_t pitch, const uint8_t *loss_mask, const fse_block *blocks, int n_blocks,
+                            float *patches, cudaStream_t stream) {
+    if (!h->pipe_ready) {
+        FSE_CUDA(h, cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking));
+        FSE_CUDA(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
+        FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming));
+        FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+        for (int c = 0; c < kHostChunks; ++c) {
+            FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming));
+            FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_k[c], cudaEventDisableTiming));
+        }
+        FSE_CUDA(h, cudaMalloc(&h->d_ccounter, kHostChunks * sizeof(int)));
+        h->pipe_ready = true;
+    }
+    const int K = std::min(kHostChunks, std::min(n_images, n_blocks));
+    int halo = 0;
+    for (int c = 0; c < h->cfg.n_classes; ++c)
+        if (h->cfg.cls[c].frames > 1) halo = std::max(halo, (h->cfg.cls[c].frames - 1) / 2);
+    // chunk c: blocks [cs[c], cs[c+1]), patches [po[c], po[c+1]), images [0, need[c]) resident
+    int cs[kHostChunks + 1], need[kHostChunks];
+    long long po[kHostChunks + 1];
+    // a full pipeline has small first and last chunks (1/16 of the blocks
+    // each: the GPU waits for the first upload, the host for the last
+    // read-back) and one large chunk between; small batches: equal chunks
+    static const int kWeight[kHostChunks] = {1, 14, 1};
+    const bool weighted = K == kHostChunks && n_blocks >= 16 * 64;
+    int wsum = 0, wacc = 0;
+    for (int c = 0; c < K; ++c) wsum += weighted ? kWeight[c] : 1;
+    for (int c = 0; c <= K; ++c) {
+        cs[c] = (int)((long long)n_blocks * wacc / wsum);
+        if (c < K) wacc += weighted ? kWeight[c] : 1;
+    }
+    long long acc = 0;
+    int hi = 0;
+    for (int c = 0; c < K; ++c) {
+        po[c] = acc;
+        for (int i = cs[c]; i < cs[c + 1]; ++i) {
+            hi = std::max(hi, std::min(n_images, blocks[i].image + halo + 1));
+            const long long b = h->cfg.cls[blocks[i].cls].block;
+            acc += b * b;
+        }
+        need[c] = hi;
+    }
+    po[K] = acc;
+    fse_status st = grow(h, &h->d_cblocks, &h->cblocks_cap, (size_t)n_blocks);
+    if (st != FSE_OK) return st;
+    if ((size_t)n_blocks > h->h_cblocks_cap) {
+        if (h->h_cblocks) cudaFreeHost(h->h_cblocks);
+        h->h_cblocks = nullptr;
+        h->h_cblocks_cap = 0;
+        FSE_CUDA(h, cudaMallocHost(&h->h_cblocks, (size_t)n_blocks * sizeof(BlockRec)));
+        h->h_cblocks_cap = n_blocks;
+    }
+    FSE_CUDA(h, cudaEventRecord(h->ev_start, stream));
+    FSE_CUDA(h, cudaStreamWaitEvent(h->h2d_stream, h->ev_start, 0));
+    FSE_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, h->ev_start, 0));
+    DevParams P{};
+    P.images = h->d_img;
+    P.dtype = dtype;
+    P.H = height;
+    P.W = width;
+    P.pitch = (long long)pitch;
+    P.mask = h->d_mask;
+    P.patches = h->d_patch;
+    P.n_images = n_images;
+    P.tr_stride = 1;
+    P.tw = h->d_tw;
+    P.err = h->d_err;
+    set_classes(h, P, false);
+    const size_t img_frame = (size_t)height * pitch, mask_frame = (size_t)height * width;
+    int copied = 0;
+    for (int c = 0; c < K; ++c) {
+        // upload what chunk c needs beyond the earlier chunks (issued before
+        // the chunk is planned, so the copy engine starts at once; from
+        // pageable memory the host waits here while chunk c-1 computes)
+        if (need[c] > copied) {
+            const size_t n = (size_t)(need[c] - copied);
+            FSE_CUDA(h, cudaMemcpyAsync(static_cast<char *>(h->d_img) + copied * img_frame,
+                                        static_cast<const char *>(images) + copied * img_frame, n * img_frame,
+                                        cudaMemcpyHostToDevice, h->h2d_stream));
+            FSE_CUDA(h, cudaMemcpyAsync(h->d_mask + copied * mask_frame, loss_mask + copied * mask_frame,
+                                        n * mask_frame, cudaMemcpyHostToDevice, h->h2d_stream));
+            copied = need[c];
+        }
+        const int n = cs[c + 1] - cs[c];
+        Plan pc;
+        st = validate_and_plan(h, h->d_img, dtype, n_images, height, width, pitch, h->d_mask, blocks + cs[c], n, pc);
+        if (st != FSE_OK) {
+            cudaStreamSynchronize(h->h2d_stream);
+            cudaStreamSynchronize(stream);
+            return st;
+        }
+        for (BlockRec &r : pc.sorted) {
+            r.orig += cs[c];
+            r.patch_off += po[c];
+        }
+        // the sorted list travels on the upload stream too: a copy on the
+        // compute stream would queue behind the next chunk's upload
+        std::memcpy(h->h_cblocks + cs[c], pc.sorted.data(), (size_t)n * sizeof(BlockRec));
+        FSE_CUDA(h, cudaMemcpyAsync(h->d_cblocks + cs[c], h->h_cblocks + cs[c], (size_t)n * sizeof(BlockRec),
+                                    cudaMemcpyHostToDevice, h->h2d_stream));
+        FSE_CUDA(h, cudaEventRecord(h->ev_in[c], h->h2d_stream));
+        P.blocks = h->d_cblocks + cs[c];
+        P.n_seg = pc.n_seg;
+        for (int sg = 0; sg < pc.n_seg; ++sg) {
+            P.seg_cls[sg] = pc.seg_cls[sg];
+            P.seg_item_end[sg] = pc.seg_item_end[sg];
+            P.seg_block_start[sg] = pc.seg_block_start[sg];
+            P.seg_block_count[sg] = pc.seg_block_count[sg];
+        }
+        P.total_items = pc.total_items;
+        P.counter = h->d_ccounter + c;
+        FSE_CUDA(h, cudaStreamWaitEvent(stream, h->ev_in[c], 0));
+        int nt = 256, cps = h->max_ctas_per_sm_256;
+        {   // the autotuner times graph replays of h->params: lend it this chunk's
+            const DevParams saved = h->params;
+            h->params = P;
+            st = autotune(h, pc, stream, &nt, &cps);
+            h->params = saved;
+            if (st != FSE_OK) return st;
+        }
+        const int grid = std::max(1, std::min(pc.total_items, cps * h->sm_count));
+        FSE_CUDA(h, cudaMemsetAsync(P.counter, 0, sizeof(int), stream));
+        launch_fse(h, nt, grid, P, stream);
+        FSE_CUDA(h, cudaGetLastError());
+        FSE_CUDA(h, cudaEventRecord(h->ev_k[c], stream));
+    }
+    // read-backs after every launch is queued (a copy to pageable memory
+    // returns only when it is done)
+    for (int c = 0; c < K; ++c) {
+        FSE_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, h->ev_k[c], 0));
+        FSE_CUDA(h, cudaMemcpyAsync(patches + po[c], h->d_patch + po[c], (size_t)(po[c + 1] - po[c]) * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->d2h_stream));
+    }
+    FSE_CUDA(h, cudaEventRecord(h->ev_out, h->d2h_stream));
+    FSE_CUDA(h, cudaStreamWaitEvent(stream, h->ev_out, 0));
+    h->last_n_blocks = n_blocks;
+    h->last_stream = stream;
+    FSE_CUDA(h, cudaStreamSynchronize(stream));
     return FSE_OK;
 }
 
@@ -883,9 +1081,9 @@ fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dty
     }
     if (!patches) return fail(h, FSE_ERR_INVALID_ARG, "patches is NULL");
     // validate before any copy (the geometry is checked again by run_batch)
-    Plan pl;
-    fse_status st = validate_and_plan(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks,
-                                      n_blocks, pl);
+    long long patch_total = 0;
+    fse_status st = validate_batch(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks,
+                                   n_blocks, &patch_total);
     if (st != FSE_OK) return st;
     const size_t img_bytes = (size_t)n_images * height * pitch_bytes;
     const size_t mask_bytes = (size_t)n_images * height * width;
@@ -893,14 +1091,18 @@ fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dty
     if (st != FSE_OK) return st;
     st = grow(h, &h->d_mask, &h->mask_cap, mask_bytes);
     if (st != FSE_OK) return st;
-    st = grow(h, &h->d_patch, &h->patch_cap, (size_t)pl.patch_total);
+    st = grow(h, &h->d_patch, &h->patch_cap, (size_t)patch_total);
     if (st != FSE_OK) return st;
+    const bool plain = h->cfg.init == FSE_INIT_ZERO && !(h->cfg.flags & (FSE_FLAG_TRACE | FSE_FLAG_ORDERED));
+    if (plain && n_images >= 2 && n_blocks >= 2)
+        return run_host_chunked(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks, n_blocks,
+                                patches, stream);
     FSE_CUDA(h, cudaMemcpyAsync(h->d_img, images, img_bytes, cudaMemcpyHostToDevice, stream));
     FSE_CUDA(h, cudaMemcpyAsync(h->d_mask, loss_mask, mask_bytes, cudaMemcpyHostToDevice, stream));
     st = run_batch(h, h->d_img, dtype, n_images, height, width, pitch_bytes, h->d_mask, blocks, n_blocks, nullptr,
                    h->d_patch, stream);
     if (st != FSE_OK) return st;
-    FSE_CUDA(h, cudaMemcpyAsync(patches, h->d_patch, (size_t)pl.patch_total * sizeof(float), cudaMemcpyDeviceToHost,
+    FSE_CUDA(h, cudaMemcpyAsync(patches, h->d_patch, (size_t)patch_total * sizeof(float), cudaMemcpyDeviceToHost,
                                 stream));
     FSE_CUDA(h, cudaStreamSynchronize(stream));
     return FSE_OK;
@@ -988,6 +1190,17 @@ void fse_destroy(fse_handle *h) {
         cudaFree(h->d_cnn_out);
         cudaFree(h->d_est);
         if (h->upload_done) cudaEventDestroy(h->upload_done);
+        cudaFree(h->d_cblocks);
+        if (h->h_cblocks) cudaFreeHost(h->h_cblocks);
+        cudaFree(h->d_ccounter);
+        for (int c = 0; c < kHostChunks; ++c) {
+            if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
+            if (h->ev_k[c]) cudaEventDestroy(h->ev_k[c]);
+        }
+        if (h->ev_start) cudaEventDestroy(h->ev_start);
+        if (h->ev_out) cudaEventDestroy(h->ev_out);
+        if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);
+        if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     }
     delete h;
