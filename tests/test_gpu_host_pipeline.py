@@ -2,8 +2,8 @@
 chunks (upload, conceal, read back on three streams).  Its patches must equal
 those of the device entry point bit for bit, whatever the order of the block
 list (image order, shuffled, blocks of the last image first), for video
-volumes (which read the neighbouring frames), for mixed block sizes, and from
-pageable or pinned host memory."""
+volumes (which read the neighbouring frames), for mixed block sizes, for FP32
+images, and from pageable or pinned host memory."""
 import numpy as np
 import pytest
 
@@ -99,7 +99,15 @@ def test_pipeline_mixed_sizes_and_few_blocks(P):
     classes = [C16, C32, C64]
     mask = synth.loss_mask(blocks, [4, 8, 16], T, H, W)
     np.testing.assert_array_equal(_host(P, classes, video, mask, blocks), _device(P, classes, video, mask, blocks))
-    # two blocks over three images: two chunks of one block each
+    # two blocks: two chunks of one block each
     two = blocks[blocks[:, 3] == 2][:2]
     m2 = synth.loss_mask(two, [4, 8, 16], T, H, W)
     np.testing.assert_array_equal(_host(P, classes, video, m2, two), _device(P, classes, video, m2, two))
+
+
+def test_pipeline_fp32_images(P):
+    video, blocks = _frames(340, 6, 96, 128, 16, 0.25)
+    video = (video.astype(np.float32) * 0.75 + 0.125).astype(np.float32)
+    mask = synth.loss_mask(blocks, [16], *video.shape)
+    np.testing.assert_array_equal(_host(P, [C64], video, mask, blocks, pinned=True),
+                                  _device(P, [C64], video, mask, blocks))
