@@ -10,7 +10,8 @@ batch (207,360 blocks) in one graph-captured persistent launch.
 Metric: lost 16x16 blocks concealed per second (higher is better).
   value  device-resident inputs, CUDA events on the launch stream
   e2e    the host-buffer C-ABI entry point: H2D of frames + mask, kernel,
-         D2H of the concealed patches, per step
+         D2H of the concealed patches, per step (pipelined inside the call:
+         uploads, launches and read-backs of three chunks overlap)
 Under torchrun every rank conceals its own 64-frame batch (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 
