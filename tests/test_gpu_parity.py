@@ -243,6 +243,46 @@ def test_full_size_throughput_config_sampled(fse):
     assert s["ok"], s
 
 
+def test_full_size_uneven_config_sampled(fse):
+    """The uneven-size launch the benchmark times (30 x 1920x1080 u8 frames,
+    3% of the samples lost in 4/8/16 blocks, F 16/32/64, I=200, one launch):
+    bit-identical with and without the trace, and 16 sampled blocks of every
+    class match the oracle (guided replay)."""
+    T, H, W = 30, 1080, 1920
+    vid = synth.make_video_torch(3030, T, H, W, device="cuda")
+    blocks = np.concatenate([synth.uneven_losses(5000 + t, H, W, image=t) for t in range(T)])
+    mask_np = synth.loss_mask(blocks, [4, 8, 16], T, H, W)
+    dmask = torch.from_numpy(mask_np).cuda()
+    cls = [C16, C32, C64]
+    sizes = np.array([c["block"] ** 2 for c in cls])[blocks[:, 3]]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    res = {}
+    for trace in (False, True):
+        eng = fse.Engine(cls, trace=trace)
+        patches = torch.zeros(int(offs[-1]), dtype=torch.float32, device="cuda")
+        eng.run(vid, dmask, blocks, patches=patches)
+        torch.cuda.synchronize()
+        res[trace] = (patches.cpu().numpy(), eng.trace()[:2] if trace else None)
+        eng.close()
+    np.testing.assert_array_equal(res[False][0], res[True][0])
+    rng = np.random.default_rng(6)
+    pick = np.sort(np.concatenate([rng.choice(np.flatnonzero(blocks[:, 3] == c), 16, replace=False)
+                                   for c in range(3)]))
+    frames = sorted(set(int(blocks[i, 0]) for i in pick))
+    host = {f: vid[f].cpu().numpy() for f in frames}
+    sel, energy = res[True][1]
+    out = []
+    for i in pick:
+        bk = blocks[i].copy()
+        f, b = int(bk[0]), cls[int(bk[3])]["block"]
+        bk[0] = 0
+        p = res[True][0][offs[i]:offs[i + 1]].reshape(b, b).astype(np.float64)
+        out.append(parity.check_block(host[f], mask_np[f], bk, cls, p, sel[i], energy[i]))
+    s = parity.summarize(out)
+    print("uneven full-size sample:", s)
+    assert s["ok"], s
+
+
 # ------------------------------------------------- model over the whole area
 @pytest.mark.parametrize("uneven", [False, True])
 def test_area_model_matches_guided_oracle(fse, uneven):
