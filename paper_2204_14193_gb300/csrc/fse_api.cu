@@ -5,7 +5,8 @@
 // first, grouped into work items of one F=64 / four F=32 / sixteen F=16
 // blocks), the CUDA-graph cache (memset of the work-queue head + one
 // persistent launch, re-captured only when the plan or a pointer changes),
-// the grid-size autotuner, and the host-buffer entry point.
+// the grid-size autotuner, and the host-buffer entry point (a pipeline of
+// chunked uploads, launches and read-backs on three streams).
 #include <cuda_runtime.h>
 
 #include <algorithm>
