@@ -313,12 +313,16 @@ void fse_cnn_destroy(fse_cnn *c);
  *   cuda_stream          stream to enqueue on; the current device is used
  * The first call on a device looks up the array's device address and the
  * kernel's occupancy (once per device); make that first call before any
- * stream capture.  All calls on a device share the array and it keeps the
+ * stream capture.  That set-up belongs to the device's context: after
+ * cudaDeviceReset on a device, do not call this entry point on it again in
+ * the same process.  All calls on a device share the array and it keeps the
  * last call's contents: each call rewrites what it reads and zeroes the
  * queue head, but calls whose GPU work overlaps (other streams or threads)
- * race on it and must be serialised by the caller.  The host block list is
- * copied from pageable memory, so the call waits for earlier work on the
- * stream before it returns.  Errors: fse_last_error(NULL).
+ * race on it and must be serialised by the caller.  The block list is copied
+ * to the device on the stream: from pageable host memory the call returns
+ * once the list has been staged, from pinned (page-locked) memory the copy
+ * is asynchronous and the array must stay valid and unchanged until the
+ * stream has reached the call.  Errors: fse_last_error(NULL).
  */
 fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, int n_classes, const void *images,
                                          int dtype, int n_images, int height, int width,

@@ -23,6 +23,8 @@
 #include "fse_cnn.cuh"
 #include "fse_cnn_tc.cuh"
 #include "fse_device.cuh"
+#include "fse_kernels.cuh"
+#include "fse_tables.cuh"
 
 using fse::BlockRec;
 using fse::DevParams;
@@ -78,8 +80,7 @@ struct fse_handle {
     fse_config cfg{};
     int device = 0;
     int sm_count = 0;
-    int max_ctas_per_sm = 1;       // of the 128-thread kernel
-    int max_ctas_per_sm_256 = 1;   // of the 256-thread kernel
+    int max_ctas[3][2] = {};       // CTAs per SM of each kernel set (fse_device.cuh) x {128, 256} threads
     size_t smem_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     float *d_wtab[FSE_MAX_CLASSES] = {};
@@ -106,6 +107,7 @@ struct fse_handle {
     DevParams params{};
     int grid = 0;
     int nt = 128;                  // threads per CTA of the captured launch
+    int ks = fse::kSetImage;       // kernel set of the captured launch
     // autotuner: chosen (threads per CTA, CTAs per SM) per class-mix signature
     std::vector<std::pair<uint64_t, std::pair<int, int>>> tuned;
     // host-buffer staging
@@ -238,6 +240,7 @@ struct Plan {
     int total_items = 0;
     long long patch_total = 0;
     uint64_t mix_sig = 0;
+    int ks = fse::kSetImage;   // kernel set that covers the batch's classes
 };
 
 // Argument checks of one batch call (geometry, every block's class and
@@ -333,6 +336,12 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         sig = fnv1a(key, sizeof key, sig);
     }
     pl.mix_sig = sig;
+    bool all_f64 = true;
+    for (int sg = 0; sg < pl.n_seg; ++sg) {
+        const fse_class &k = cfg.cls[pl.seg_cls[sg]];
+        all_f64 = all_f64 && k.fft == 64 && k.frames <= 1;
+    }
+    pl.ks = fse::kernel_set_for(h->ext, all_f64);
     return FSE_OK;
 }
 
@@ -357,16 +366,13 @@ void set_classes(const fse_handle *h, DevParams &P, bool learned) {
     }
 }
 
-// The persistent concealment kernel of a handle: 128 or 256 threads per CTA,
-// the image-only or the extended instantiation.
-void launch_fse(const fse_handle *h, int nt, int grid, const DevParams &P, cudaStream_t s) {
-    if (nt == 256)
-        h->ext ? fse::fse_batch_kernel<256, true><<<grid, 256, h->smem_bytes, s>>>(P)
-               : fse::fse_batch_kernel<256, false><<<grid, 256, h->smem_bytes, s>>>(P);
-    else
-        h->ext ? fse::fse_batch_kernel<128, true><<<grid, 128, h->smem_bytes, s>>>(P)
-               : fse::fse_batch_kernel<128, false><<<grid, 128, h->smem_bytes, s>>>(P);
+// The persistent concealment kernel of a handle: kernel set ks, 128 or 256
+// threads per CTA.
+cudaError_t launch_fse(const fse_handle *h, int ks, int nt, int grid, const DevParams &P, cudaStream_t s) {
+    return fse::batch_kernel_launch(ks, nt, grid, h->smem_bytes, s, P);
 }
+
+int ctas_per_sm(const fse_handle *h, int ks, int nt) { return h->max_ctas[ks][nt == 256 ? 1 : 0]; }
 
 template <typename T>
 fse_status grow(fse_handle *h, T **ptr, size_t *cap, size_t need) {
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(256) area_model_kernel(const DevParams P, floa
     }
 }
 
-fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) {
+fse_status capture_graph(fse_handle *h, int ks, int nt, int grid, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     FSE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     if (h->learned_launch && h->tc_net) {
@@ -500,8 +506,7 @@ fse_status capture_graph(fse_handle *h, int nt, int grid, cudaGraphExec_t *out) 
     }
     if (h->params.ordered) cudaMemsetAsync(h->d_done, 0, (size_t)h->ordered_n * sizeof(int), h->cap_stream);
     cudaMemsetAsync(h->params.counter, 0, sizeof(int), h->cap_stream);
-    launch_fse(h, nt, grid, h->params, h->cap_stream);
-    cudaError_t le = cudaGetLastError();
+    cudaError_t le = launch_fse(h, ks, nt, grid, h->params, h->cap_stream);
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
     if (le != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -525,7 +530,7 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
             *best_cps = kv.second.second;
             return FSE_OK;
         }
-    int bnt = 256, bcps = h->max_ctas_per_sm_256;
+    int bnt = 256, bcps = ctas_per_sm(h, pl.ks, 256);
     // small batches cannot fill the machine: no measurement needed
     if ((long long)pl.total_items >= 2LL * h->sm_count) {
         cudaEvent_t e0, e1;
@@ -533,11 +538,11 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
         FSE_CUDA(h, cudaEventCreate(&e1));
         float best_ms = 1e30f;
         for (int nt : {128, 256}) {
-            const int maxc = nt == 256 ? h->max_ctas_per_sm_256 : h->max_ctas_per_sm;
+            const int maxc = ctas_per_sm(h, pl.ks, nt);
             for (int cps = std::max(1, maxc - 1); cps <= maxc; ++cps) {
                 const int grid = std::min(pl.total_items, cps * h->sm_count);
                 cudaGraphExec_t ex = nullptr;
-                fse_status st = capture_graph(h, nt, grid, &ex);
+                fse_status st = capture_graph(h, pl.ks, nt, grid, &ex);
                 if (st != FSE_OK) return st;
                 cudaGraphLaunch(ex, stream);  // warm-up
                 cudaEventRecord(e0, stream);
@@ -749,12 +754,13 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         P.done = h->d_done;
         h->ordered_n = n_blocks;
     }
-    int nt = 256, cps = h->max_ctas_per_sm_256;
+    int nt = 256, cps = ctas_per_sm(h, pl.ks, 256);
     st = autotune(h, pl, stream, &nt, &cps);
     if (st != FSE_OK) return st;
     h->nt = nt;
+    h->ks = pl.ks;
     h->grid = std::max(1, std::min(pl.total_items, cps * h->sm_count));
-    st = capture_graph(h, nt, h->grid, &h->gexec);
+    st = capture_graph(h, pl.ks, nt, h->grid, &h->gexec);
     if (st != FSE_OK) return st;
     h->graph_valid = true;
     h->plan_key = key;
@@ -889,7 +895,7 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         P.total_items = pc.total_items;
         P.counter = h->d_ccounter + c;
         FSE_CUDA(h, cudaStreamWaitEvent(stream, h->ev_in[c], 0));
-        int nt = 256, cps = h->max_ctas_per_sm_256;
+        int nt = 256, cps = ctas_per_sm(h, pc.ks, 256);
         {   // the autotuner times graph replays of h->params: lend it this chunk's
             const DevParams saved = h->params;
             h->params = P;
@@ -899,8 +905,7 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         }
         const int grid = std::max(1, std::min(pc.total_items, cps * h->sm_count));
         FSE_CUDA(h, cudaMemsetAsync(P.counter, 0, sizeof(int), stream));
-        launch_fse(h, nt, grid, P, stream);
-        FSE_CUDA(h, cudaGetLastError());
+        FSE_CUDA(h, launch_fse(h, pc.ks, nt, grid, P, stream));
         FSE_CUDA(h, cudaEventRecord(h->ev_k[c], stream));
     }
     // read-backs after every launch is queued (a copy to pageable memory
@@ -958,25 +963,19 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     h->smem_bytes = smem;
     h->ext = (cfg->flags & FSE_FLAG_ORDERED) != 0;
     for (int c = 0; c < cfg->n_classes; ++c) h->ext = h->ext || cfg->cls[c].frames > 1;
-    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    CREATE_CUDA(cudaFuncSetAttribute(fse::fse_batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-    int occ = 0, occ2 = 0;
-    if (h->ext) {
-        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128, true>, 128, smem));
-        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fse::fse_batch_kernel<256, true>, 256, smem));
-    } else {
-        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, smem));
-        CREATE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, fse::fse_batch_kernel<256>, 256, smem));
+    // the kernel sets this handle's batches can run: the extended set, or the
+    // image set and (with an FFT-64 class) the FFT-64 set
+    bool any64 = false;
+    for (int c = 0; c < cfg->n_classes; ++c) any64 = any64 || cfg->cls[c].fft == 64;
+    for (int ks : {fse::kSetImage, fse::kSetExt, fse::kSetF64}) {
+        if ((ks == fse::kSetExt) != h->ext || (ks == fse::kSetF64 && !any64)) continue;
+        for (int t = 0; t < 2; ++t) {
+            int occ = 0;
+            CREATE_CUDA(fse::batch_kernel_prepare(ks, t ? 256 : 128, smem, &occ));
+            if (occ < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
+            h->max_ctas[ks][t] = occ;
+        }
     }
-    if (occ < 1 || occ2 < 1) return bail(fail(h, FSE_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
-    h->max_ctas_per_sm = occ;
-    h->max_ctas_per_sm_256 = occ2;
     h->tc_net = cfg->init == FSE_INIT_LEARNED && cfg->cls[0].block == 16 && cfg->cls[0].border == 16;
     if (h->tc_net) {
         if (prop.major < 10) return bail(fail(h, FSE_ERR_UNSUPPORTED, "learned initialisation needs sm_100 or later"));

@@ -203,6 +203,9 @@ __host__ __device__ constexpr int cta_region_bytes(int F) { return F == 64 ? 16 
 
 constexpr int kMaxWarps = 8;
 
+// kernel sets of fse_batch_kernel (see there)
+constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2;
+
 struct RedShared {
     uint4 win[2][kMaxWarps];   // per-warp argmax candidates, double-buffered by iteration parity
     float sum[kMaxWarps];
@@ -346,26 +349,39 @@ __device__ __forceinline__ bool search_quartet(const uint64_t *Rre, const uint64
     return false;
 }
 
-// Search all bins of this thread for energy M (the thread's max equals M).
-// Quartets are checked in order, so the first hit has the smallest linear
-// index.  Returns the local slot (2 i + h) or -1, with the residual there.
+// Search the bins of this thread for energy M (the thread's max equals M).
+// jb is the first quartet whose maximum equals the thread's maximum (carried
+// out of the update), so the first hit inside it has the smallest linear
+// index of the thread.  Returns the local slot (2 i + h) or -1, with the
+// residual there.
 template <int NQ>
-__device__ __forceinline__ int thread_search(const uint64_t *Rre, const uint64_t *Rim, const float *q,
-                                             uint32_t M, float &rr, float &ri) {
+__device__ __forceinline__ int thread_search(const uint64_t *Rre, const uint64_t *Rim, int jb, uint32_t M,
+                                             float &rr, float &ri) {
     int hit = -1;
-    bool done = false;
-    if (__float_as_uint(q[0]) == M) done = search_quartet<0>(Rre, Rim, M, hit, rr, ri);
-    if (!done && __float_as_uint(q[1]) == M) done = search_quartet<1>(Rre, Rim, M, hit, rr, ri);
+    if (jb == 0) search_quartet<0>(Rre, Rim, M, hit, rr, ri);
+    else if (jb == 1) search_quartet<1>(Rre, Rim, M, hit, rr, ri);
     if constexpr (NQ > 2) {
-        if (!done && __float_as_uint(q[2]) == M) done = search_quartet<2>(Rre, Rim, M, hit, rr, ri);
-        if (!done && __float_as_uint(q[3]) == M) done = search_quartet<3>(Rre, Rim, M, hit, rr, ri);
+        if (jb == 2) search_quartet<2>(Rre, Rim, M, hit, rr, ri);
+        else if (jb == 3) search_quartet<3>(Rre, Rim, M, hit, rr, ri);
     }
     return hit;
 }
 
+// Running maximum over the quartets of a thread with the index of the first
+// quartet that holds it (the strict comparison keeps the first).
+__device__ __forceinline__ void quartet_max(int j, float qj, float &tmax, int &jb) {
+    if (j == 0) {
+        tmax = qj;
+        jb = 0;
+    } else {
+        jb = qj > tmax ? j : jb;
+        tmax = fmaxf(tmax, qj);
+    }
+}
+
 // Group-wide argmax of |R_w|^2 with ties to the smallest linear index.
-// tmax: this thread's max energy; q: its quartet maxima; parity: iteration
-// parity (double-buffers the cross-warp exchange).
+// tmax: this thread's max energy; jb: the first quartet holding it; parity:
+// iteration parity (double-buffers the cross-warp exchange).
 //
 // Every warp-wide step (shuffle, redux, shared-memory exchange) waits in the
 // SM's memory-instruction queue behind the residual update's 16-byte loads,
@@ -373,8 +389,8 @@ __device__ __forceinline__ int thread_search(const uint64_t *Rre, const uint64_t
 // one redux.sync for the max, the owner's register search, one redux.sync for
 // the smallest index, and (multi-warp groups) one shared-memory exchange.
 template <int F, int PAIRS, int NT, int FT = 1>
-__device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t *Rim, float tmax,
-                                             const float *q, const Grp &gr, RedShared *rs, int parity) {
+__device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t *Rim, float tmax, int jb,
+                                             const Grp &gr, RedShared *rs, int parity) {
     using G = Geo<F, PAIRS, FT>;
     const uint32_t mt = __float_as_uint(tmax);
     const int c0 = gr.lt % G::LPR, r0 = gr.lt / G::LPR;
@@ -393,7 +409,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         uint32_t cand = 0xffffffffu;
         float rr = 0.f, ri = 0.f;
         if (mt == mw) {
-            const int hit = thread_search<G::NQ>(Rre, Rim, q, mw, rr, ri);
+            const int hit = thread_search<G::NQ>(Rre, Rim, jb, mw, rr, ri);
             if (hit >= 0) cand = lin(hit);
         }
         const uint32_t iw = __reduce_min_sync(0xffffffffu, cand);
@@ -423,7 +439,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         uint32_t cand = 0xffffffffu;
         float rr = 0.f, ri = 0.f;
         if (mt == M) {
-            const int hit = thread_search<G::NQ>(Rre, Rim, q, M, rr, ri);
+            const int hit = thread_search<G::NQ>(Rre, Rim, jb, M, rr, ri);
             if (hit >= 0) cand = lin(hit);
         }
         uint32_t iw = 0xffffffffu;
@@ -616,20 +632,19 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     const float cg = C.gamma * W0bar;
 
     // ---- S5: first selection (energies of R_w^(0)) ----
-    float q[NQ];
     float tmax = 0.f;
+    int jb = 0;
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
         const uint64_t e0 = energy2(Rre[4 * j], Rim[4 * j]), e1 = energy2(Rre[4 * j + 1], Rim[4 * j + 1]);
         const uint64_t e2 = energy2(Rre[4 * j + 2], Rim[4 * j + 2]), e3 = energy2(Rre[4 * j + 3], Rim[4 * j + 3]);
         const float a = max3f(lo_of(e0), hi_of(e0), lo_of(e1));
         const float bq = max3f(hi_of(e1), lo_of(e2), hi_of(e2));
-        q[j] = max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3)));
-        tmax = fmaxf(tmax, q[j]);
+        quartet_max(j, max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3))), tmax, jb);
     }
     const int iters = C.iters;
     Pick pick;
-    if (iters > 0) pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, 0);
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, jb, gr, rsh, 0);
 
     const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
     for (int nu = 1; nu <= iters; ++nu) {
@@ -693,12 +708,11 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             }
             const float a = max3f(ev[0], ev[1], ev[2]);
             const float bq = max3f(ev[3], ev[4], ev[5]);
-            q[j] = max3f(a, bq, fmaxf(ev[6], ev[7]));
-            tmax = fmaxf(tmax, q[j]);
+            quartet_max(j, max3f(a, bq, fmaxf(ev[6], ev[7])), tmax, jb);
         }
         model();
         // ---- S5: next selection ----
-        pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, q, gr, rsh, nu & 1);
+        pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, jb, gr, rsh, nu & 1);
     }
 
     // ---- S10: write Re{g} on B ----
@@ -900,20 +914,19 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     const float cg = C.gamma * W0bar;
 
     // ---- S5: first selection (energies of R_w^(0)) ----
-    float q[NQ];
     float tmax = 0.f;
+    int jb = 0;
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
         const uint64_t e0 = energy2(Rre[4 * j], Rim[4 * j]), e1 = energy2(Rre[4 * j + 1], Rim[4 * j + 1]);
         const uint64_t e2 = energy2(Rre[4 * j + 2], Rim[4 * j + 2]), e3 = energy2(Rre[4 * j + 3], Rim[4 * j + 3]);
         const float a = max3f(lo_of(e0), hi_of(e0), lo_of(e1));
         const float bq = max3f(hi_of(e1), lo_of(e2), hi_of(e2));
-        q[j] = max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3)));
-        tmax = fmaxf(tmax, q[j]);
+        quartet_max(j, max3f(a, bq, fmaxf(lo_of(e3), hi_of(e3))), tmax, jb);
     }
     const int iters = C.iters;
     Pick pick;
-    if (iters > 0) pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, q, gr, rsh, 0);
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, jb, gr, rsh, 0);
 
     const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
     for (int nu = 1; nu <= iters; ++nu) {
@@ -990,12 +1003,11 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
             }
             const float a = max3f(ev[0], ev[1], ev[2]);
             const float bq = max3f(ev[3], ev[4], ev[5]);
-            q[j] = max3f(a, bq, fmaxf(ev[6], ev[7]));
-            tmax = fmaxf(tmax, q[j]);
+            quartet_max(j, max3f(a, bq, fmaxf(ev[6], ev[7])), tmax, jb);
         }
         model();
         // ---- S5: next selection ----
-        pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, q, gr, rsh, nu & 1);
+        pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, jb, gr, rsh, nu & 1);
     }
 
     // ---- S10: write Re{g} on B ----
@@ -1036,12 +1048,16 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
 
 // ------------------------------------------------------ persistent kernel
 // NT threads per CTA (128 or 256), up to 71 KB of dynamic shared memory, at
-// most three CTAs per SM.  EXT: compiled with video volumes and ordered
-// concealment (batches of image classes alone run the variant without them,
-// whose register allocation and code they do not burden).
-template <int NT, bool EXT = false>
+// most three CTAs per SM.  KS selects what the instantiation carries:
+//   kSetImage  image classes of every FFT size (16, 32, 64)
+//   kSetExt    also video volumes and ordered concealment
+//   kSetF64    image classes of FFT size 64 only
+// A batch runs the smallest set that covers its classes, so the code and
+// register allocation of the common cases are not burdened by the others.
+template <int NT, int KS>
 __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant__ DevParams P) {
     constexpr int PAIRS = 2048 / NT;
+    constexpr bool EXT = KS == kSetExt;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ float2 s_tw[64];
     __shared__ int s_item;
@@ -1064,6 +1080,8 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
                 if (C.F == 32) process_class<32, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh);
                 else process_class<16, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh);
             }
+        } else if constexpr (KS == kSetF64) {
+            process_class<64, PAIRS, NT, 1, false>(P, C, first, count, smem, s_tw, &rsh);
         } else {
             switch (C.F) {
                 case 64: process_class<64, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
@@ -1073,27 +1091,6 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
         }
         __syncthreads();
     }
-}
-
-// Eq. (3) weight table of one class, evaluated in FP64 and rounded once; for
-// a volume of T frames the distance includes the frame offset from the
-// centre frame (T = 1: the area's table).
-__global__ void weight_table_kernel(float *wtab, int M, int T, double rho) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T * M * M) return;
-    const int tau = i / (M * M), m = (i / M) % M, n = i % M;
-    const double cm = 0.5 * (M - 1), ct = 0.5 * (T - 1);
-    const double dist = sqrt((tau - ct) * (tau - ct) + (m - cm) * (m - cm) + (n - cm) * (n - cm));
-    wtab[i] = (float)pow(rho, dist);
-}
-
-// (cos, sin)(2 pi t / 64), FP64 then rounded once.
-__global__ void twiddle_kernel(float2 *tw) {
-    const int t = threadIdx.x;
-    if (t >= 64) return;
-    double s, c;
-    sincospi((double)t / 32.0, &s, &c);
-    tw[t] = make_float2((float)c, (float)s);
 }
 
 }  // namespace fse

@@ -17,7 +17,9 @@
 // device share it and it keeps the last call's contents, so calls whose work
 // overlaps on the GPU (other streams, other host threads) race on it and must
 // be serialised by the caller.  Each call rewrites every part it reads and
-// zeroes the work-queue head before the kernel starts.
+// zeroes the work-queue head before the kernel starts.  The persistent kernel
+// itself is the library's (fse_kernels.cuh); the table kernels are a private
+// copy (fse_tables.cuh, internal linkage).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,10 +28,8 @@
 #include <mutex>
 
 #include "fse.h"
-
-namespace {
-#include "fse_device.cuh"   // private copy of the kernels (internal linkage)
-}
+#include "fse_kernels.cuh"
+#include "fse_tables.cuh"
 
 void fse_internal_set_global_error(const char *msg);   // fse_api.cu: text of fse_last_error(NULL)
 
@@ -56,7 +56,7 @@ static __device__ __align__(256) unsigned char g_scratch[kNoallocScratchBytes];
 struct DeviceScratch {
     unsigned char *ptr = nullptr;
     int sm_count = 0;
-    int ctas_per_sm = 0;
+    int ctas_per_sm[3] = {};   // per kernel set (fse_device.cuh), 128 threads per CTA
 };
 constexpr int kMaxDevices = 64;
 DeviceScratch g_dev[kMaxDevices];
@@ -67,14 +67,20 @@ fse_status fail(fse_status st, const char *msg) {
     return st;
 }
 
+// First queue position of each class's blocks, passed to the bucketing
+// kernel by value.
+struct Starts {
+    int v[FSE_MAX_CLASSES];
+};
+
 // Bucket the caller's blocks by class into the queue order of the plan:
 // warp c walks the list 32 blocks at a time and appends the blocks of class c
 // (ballot + popcount keeps the caller's order inside the class).
-__global__ void noalloc_bucket_kernel(const fse_block *raw, int n, fse::BlockRec *rec, const int *seg_start_by_cls,
+__global__ void noalloc_bucket_kernel(const fse_block *raw, int n, fse::BlockRec *rec, const Starts starts,
                                       int n_classes) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (c >= n_classes) return;
-    int pos = seg_start_by_cls[c];
+    int pos = starts.v[c];
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         fse_block b = {0, 0, 0, -1};
@@ -153,16 +159,16 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess || !p) return fail(FSE_ERR_CUDA, "noalloc: cudaGetSymbolAddress(g_scratch) failed");
-            if (cudaFuncSetAttribute(fse::fse_batch_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNoallocSmem) !=
-                cudaSuccess)
-                return fail(FSE_ERR_CUDA, "noalloc: cannot set the kernel's shared-memory size");
-            int occ = 0, sms = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fse::fse_batch_kernel<128>, 128, kNoallocSmem) !=
-                    cudaSuccess ||
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ < 1)
-                return fail(FSE_ERR_CUDA, "noalloc: occupancy query failed");
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return fail(FSE_ERR_CUDA, "noalloc: device query failed");
+            for (int ks : {fse::kSetImage, fse::kSetF64}) {
+                int occ = 0;
+                if (fse::batch_kernel_prepare(ks, 128, kNoallocSmem, &occ) != cudaSuccess || occ < 1)
+                    return fail(FSE_ERR_CUDA, "noalloc: cannot set the kernel's shared-memory size or occupancy");
+                d.ctas_per_sm[ks] = occ;
+            }
             d.sm_count = sms;
-            d.ctas_per_sm = occ;
             d.ptr = static_cast<unsigned char *>(p);
         }
         ds = d;
@@ -195,6 +201,9 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
         pos += cnt[c];
     }
     P.total_items = items;
+    bool all_f64 = true;
+    for (int sg = 0; sg < P.n_seg; ++sg) all_f64 = all_f64 && classes[P.seg_cls[sg]].fft == 64;
+    const int ks = fse::kernel_set_for(false, all_f64);
     P.images = images;
     P.dtype = dtype;
     P.n_images = n_images;
@@ -234,18 +243,13 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
     if (cudaMemcpyAsync(d_raw, blocks, (size_t)n_blocks * sizeof(fse_block), cudaMemcpyHostToDevice, stream) !=
         cudaSuccess)
         return fail(FSE_ERR_CUDA, "noalloc: block-list copy failed");
-    // class -> segment start lives in the kernel argument (by value)
-    struct Starts { int v[FSE_MAX_CLASSES]; } st;
+    // class -> segment start travels in the kernel argument (by value)
+    Starts st;
     for (int c = 0; c < FSE_MAX_CLASSES; ++c) st.v[c] = seg_start_by_cls[c];
-    // copy the four starts next to the counter (bytes 16..31 of the scratch)
-    int *d_starts = d_counter + 4;
-    if (cudaMemcpyAsync(d_starts, st.v, sizeof st.v, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-        return fail(FSE_ERR_CUDA, "noalloc: plan copy failed");
-    noalloc_bucket_kernel<<<1, 32 * FSE_MAX_CLASSES, 0, stream>>>(d_raw, n_blocks, d_rec, d_starts, n_classes);
+    noalloc_bucket_kernel<<<1, 32 * FSE_MAX_CLASSES, 0, stream>>>(d_raw, n_blocks, d_rec, st, n_classes);
     noalloc_setup_kernel<<<1, 1, 0, stream>>>(d_counter);
-    const int grid = std::max(1, std::min(items, ds.ctas_per_sm * ds.sm_count));
-    fse::fse_batch_kernel<128><<<grid, 128, kNoallocSmem, stream>>>(P);
-    cudaError_t le = cudaGetLastError();
-    if (le != cudaSuccess) return fail(FSE_ERR_CUDA, "noalloc: kernel launch failed");
+    const int grid = std::max(1, std::min(items, ds.ctas_per_sm[ks] * ds.sm_count));
+    if (fse::batch_kernel_launch(ks, 128, grid, kNoallocSmem, stream, P) != cudaSuccess)
+        return fail(FSE_ERR_CUDA, "noalloc: kernel launch failed");
     return FSE_OK;
 }
