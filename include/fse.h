@@ -330,6 +330,15 @@ fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, int n_classes
                                          const fse_block *blocks, int n_blocks, float *out,
                                          void *cuda_stream);
 
+/* Measurement helper (no counterpart in the paper): the shared-memory load
+ * bandwidth of `device` in GB/s (1e9 bytes/s), measured as a stream of
+ * conflict-free 16-byte shared-memory loads on every SM (one CTA of 1024
+ * threads per SM), best of five event-timed launches.  This is the peak the
+ * concealment kernel's iterations, which read one 16-byte W chunk per
+ * register pair from shared memory, are reported against.  Synchronous;
+ * allocates a few bytes of device memory.  Errors: fse_last_error(NULL). */
+fse_status fse_measure_smem_bandwidth(int device, double *gbytes_per_s);
+
 /* Reason for the last failure on h (or, when h is NULL, of fse_create or
  * fse_extrapolate_batch_noalloc); never NULL; valid until the next call. */
 const char *fse_last_error(const fse_handle *h);

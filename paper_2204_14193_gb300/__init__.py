@@ -18,6 +18,7 @@ from . import _build
 
 __all__ = ["fse_class", "fse_config", "fse_block", "FseError", "fse_create", "fse_extrapolate_batch",
            "fse_extrapolate_batch_host", "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_last_error", "fse_destroy", "Engine",
+           "fse_measure_smem_bandwidth",
            "library_path", "FSE_DTYPE_U8", "FSE_DTYPE_F32", "FSE_FLAG_TRACE", "FSE_INIT_ZERO",
            "FSE_INIT_LEARNED"]
 
@@ -82,6 +83,8 @@ def _load():
             lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
                                                           c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
+            lib.fse_measure_smem_bandwidth.argtypes = [c_int, ctypes.POINTER(ctypes.c_double)]
+            lib.fse_measure_smem_bandwidth.restype = c_int
             lib.fse_last_error.argtypes = [vp]
             lib.fse_last_error.restype = ctypes.c_char_p
             lib.fse_destroy.argtypes = [vp]
@@ -207,6 +210,13 @@ def fse_get_area_model(h, model: int, model_stride: int, stream: int | None) -> 
 
 def fse_sync(h) -> None:
     _check(_load().fse_sync(h), h)
+
+
+def fse_measure_smem_bandwidth(device: int = 0) -> float:
+    """Measured shared-memory load bandwidth of the device in GB/s."""
+    out = ctypes.c_double(0.0)
+    _check(_load().fse_measure_smem_bandwidth(device, ctypes.byref(out)), None)
+    return float(out.value)
 
 
 def fse_destroy(h) -> None:

@@ -417,14 +417,20 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         if ((cand == iw && cand != 0xffffffffu) || (iw == 0xffffffffu && lane == 0))
             win[warp] = make_uint4(mw, iw, __float_as_uint(rr), __float_as_uint(ri));
         gsync<F, PAIRS, NT, FT>(gr);
-        p.idx = 0xffffffffu; p.rr = 0.f; p.ri = 0.f; p.ebits = 0u;
+        // the warps' candidates combined as a tree (log2 WPG dependent steps;
+        // the order (larger energy, then smaller index) is total, so any
+        // combination order gives the same pick)
+        uint4 e[G::WPG];
 #pragma unroll
-        for (int i = 0; i < G::WPG; ++i) {
-            const uint4 e = win[w0 + i];
-            if (e.x > p.ebits || (e.x == p.ebits && e.y < p.idx)) {
-                p.ebits = e.x; p.idx = e.y; p.rr = __uint_as_float(e.z); p.ri = __uint_as_float(e.w);
-            }
-        }
+        for (int i = 0; i < G::WPG; ++i) e[i] = win[w0 + i];
+        auto better = [](const uint4 &a, const uint4 &b) {
+            return (b.x > a.x || (b.x == a.x && b.y < a.y)) ? b : a;
+        };
+#pragma unroll
+        for (int s = 1; s < G::WPG; s <<= 1)
+#pragma unroll
+            for (int i = 0; i + s < G::WPG; i += 2 * s) e[i] = better(e[i], e[i + s]);
+        p.ebits = e[0].x; p.idx = e[0].y; p.rr = __uint_as_float(e[0].z); p.ri = __uint_as_float(e[0].w);
     } else {
         constexpr int W = G::LANES;               // lanes of one group (8, 16 or 32)
         constexpr int NG = 32 / W;                // groups per warp
