@@ -7,6 +7,7 @@
 // persistent launch, re-captured only when the plan or a pointer changes),
 // the grid-size autotuner, and the host-buffer entry point (a pipeline of
 // chunked uploads, launches and read-backs on three streams).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -366,6 +367,58 @@ void set_classes(const fse_handle *h, DevParams &P, bool learned) {
     }
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link
+// against the driver library); nullptr when unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// TMA gather of the F = 64 windows (fse_device.cuh): tensor maps over the
+// 8-bit images and the mask as [n_images * height rows, width columns], box
+// (roundup16(M) + 16) columns x M rows.  Used when the batch runs the FFT-64
+// kernel set and the buffers meet the tensor-map rules (16-byte aligned
+// bases, row pitches multiples of 16 bytes); otherwise P.tma stays 0 and the
+// kernel reads the windows with plain loads.
+void setup_tma(const fse_handle *h, DevParams &P, int ks, int dtype, const void *images, const uint8_t *mask,
+               int n_images, int height, int width, size_t pitch) {
+    P.tma = 0;
+    if (ks != fse::kSetF64 || dtype != FSE_DTYPE_U8) return;
+    if ((reinterpret_cast<uintptr_t>(images) & 15) || (reinterpret_cast<uintptr_t>(mask) & 15) || (pitch & 15) ||
+        (width & 15) || (long long)n_images * height >= (1LL << 31))
+        return;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return;
+    int maxM = 0;
+    for (int c = 0; c < h->cfg.n_classes; ++c)
+        if (h->cfg.cls[c].fft == 64) maxM = std::max(maxM, h->cfg.cls[c].block + 2 * h->cfg.cls[c].border);
+    const int bw = ((maxM + 15) & ~15) + 16, bh = maxM;
+    if (2 * (((bw * bh) + 127) & ~127) > fse::kTmaStageMax) return;
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)n_images * height};
+    const cuuint64_t istride[1] = {(cuuint64_t)pitch}, mstride[1] = {(cuuint64_t)width};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh}, es[2] = {1, 1};
+    if (enc(&P.tm_img, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(images), dims, istride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&P.tm_mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(mask), dims, mstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    P.tma = 1;
+    P.tma_bw = bw;
+    P.tma_bh = bh;
+}
+
 // The persistent concealment kernel of a handle: kernel set ks, 128 or 256
 // threads per CTA.
 cudaError_t launch_fse(const fse_handle *h, int ks, int nt, int grid, const DevParams &P, cudaStream_t s) {
@@ -704,6 +757,7 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     P.total_items = pl.total_items;
     set_classes(h, P, learned);
     P.n_images = n_images;
+    setup_tma(h, P, pl.ks, dtype, images, mask, n_images, height, width, pitch);
     P.counter = h->d_counter;
     P.tr_sel = trace ? h->d_tr_sel : nullptr;
     P.tr_energy = trace ? h->d_tr_energy : nullptr;
@@ -894,6 +948,7 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         }
         P.total_items = pc.total_items;
         P.counter = h->d_ccounter + c;
+        setup_tma(h, P, pc.ks, dtype, h->d_img, h->d_mask, n_images, height, width, pitch);
         FSE_CUDA(h, cudaStreamWaitEvent(stream, h->ev_in[c], 0));
         int nt = 256, cps = ctas_per_sm(h, pc.ks, 256);
         {   // the autotuner times graph replays of h->params: lend it this chunk's

@@ -27,8 +27,10 @@
 //   consecutive chunks, so a warp's LDS.128 is free of bank conflicts.
 #pragma once
 
-#include <cstdint>
+#include <cuda.h>   // CUtensorMap (the type only; no driver-API calls here)
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 namespace fse {
 
@@ -82,6 +84,12 @@ struct DevParams {
     const int *nb_start, *nb_list;    // CSR: earlier blocks whose B meets the block's area
     int *done;                        // per block: concealed output visible (zeroed per launch)
     int *err;                         // device status word (a bounded wait expired: 5)
+    // F = 64 windows of 8-bit images fetched as tiles by the tensor-memory
+    // accelerator: 2-D maps over [n_images * H rows, W columns] of the images
+    // and the mask, box tma_bw columns x tma_bh rows (tma = 0: plain loads)
+    int tma;
+    int tma_bw, tma_bh;
+    CUtensorMap tm_img, tm_mask;
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -169,6 +177,12 @@ __device__ __forceinline__ void dftR(float2 *x) {
 // holds NT / TB = 4096 / F^2 blocks whatever NT is.
 //   NT = 128 (16 pairs): F=64 -> 4 warps, F=32 -> 1 warp, F=16 -> 8 lanes
 //   NT = 256 ( 8 pairs): F=64 -> 8 warps, F=32 -> 2 warps, F=16 -> 16 lanes
+// The window tiles of an F = 64 block (TMA gather, below) are staged at this
+// offset of its region: after the padded FFT buffer, which the gather writes
+// while it reads them; the W chunks overwrite both later.
+constexpr int kTmaStage = 40960;
+constexpr int kTmaStageMax = 16384;   // two tiles of at most 128 x 64 bytes
+
 template <int F, int PAIRS, int FT = 1>
 struct Geo {
     static constexpr int TB = FT * F * F / (2 * PAIRS);   // threads per block
@@ -195,6 +209,8 @@ struct Geo {
     static_assert(FT == 1 || F % RSTEP == 0, "a thread's rows repeat in every temporal plane");
     static_assert(!RUNS || PAIRS % 8 == 0, "runs of 8 rows");
     static_assert(REGION >= 8 * FT * F * FP, "the FFT buffer fits the region");
+    static_assert(!RUNS || (kTmaStage >= 8 * F * FP && kTmaStage + kTmaStageMax <= REGION),
+                  "the TMA staging area lies between the FFT buffer and the end of the region");
 };
 
 // dynamic shared memory of one CTA working on blocks of FFT size F (one
@@ -209,7 +225,52 @@ constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2;
 struct RedShared {
     uint4 win[2][kMaxWarps];   // per-warp argmax candidates, double-buffered by iteration parity
     float sum[kMaxWarps];
+    unsigned long long mbar;   // completion barrier of the window tiles (TMA gather)
 };
+
+// ------------------------------------------------ TMA gather of a window
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 2-D tiled TMA load of the box at (x, y) (x: innermost, in elements) into
+// shared memory, completing on bar
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Wait for phase `parity` of bar, bounded by 1 s of %globaltimer; false if
+// the wait ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (int spin = 0;; ++spin) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (spin == 0) t0 = t;
+        else if (t - t0 > 1000000000ull) return false;
+    }
+}
 
 struct Grp {
     int g;            // group index inside the CTA
@@ -471,7 +532,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 // variant that covers b*b).  EXT: built with ordered concealment.
 template <int F, int PAIRS, int NT, int NP, bool EXT = false>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
-                                        unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
+                                        unsigned char *smem, const float2 *s_tw, RedShared *rsh, uint32_t &tph) {
     using G = Geo<F, PAIRS>;
     constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
     Grp gr;
@@ -515,15 +576,43 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     constexpr int NPOS = F * F / TB;
     float sv[NPOS];
     uint8_t mk[NPOS];
+    if (G::RUNS && P.tma) {
+        // 8-bit F = 64 windows: the image and mask tiles of the M x M area
+        // arrive in shared memory by two TMA copies.  The tile's first column
+        // is the area's first column rounded down to a 16-byte boundary (xs
+        // columns before it); rows and columns outside the images read 0 and
+        // are excluded below like in the plain gather.
+        unsigned char *stage = region + kTmaStage;
+        const int bw = P.tma_bw, bh = P.tma_bh, moff = (bw * bh + 127) & ~127;
+        const int gx = blk.x - d, x0 = gx & ~15, xs = gx - x0;
+        if (lt == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&rsh->mbar, 2u * (uint32_t)(bw * bh));
+            tma_load_2d(stage, &P.tm_img, x0, blk.image * P.H + blk.y - d, &rsh->mbar);
+            tma_load_2d(stage + moff, &P.tm_mask, x0, blk.image * P.H + blk.y - d, &rsh->mbar);
+        }
+        if (!mbar_wait(&rsh->mbar, tph)) atomicExch(P.err, 5);
+        tph ^= 1u;
 #pragma unroll
-    for (int t = 0; t < NPOS; ++t) {
-        const int pix = lt + t * TB;
-        const int yy = min(max(blk.y - d + pix / F - off, 0), P.H - 1);
-        const int xx = min(max(blk.x - d + pix % F - off, 0), P.W - 1);
-        mk[t] = P.mask[((size_t)blk.image * P.H + yy) * P.W + xx];
-        const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
-        sv[t] = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
-                             : reinterpret_cast<const float *>(row)[xx];
+        for (int t = 0; t < NPOS; ++t) {
+            const int pix = lt + t * TB;
+            const int am = pix / F - off, an = pix % F - off;
+            const bool in = am >= 0 && am < M && an >= 0 && an < M;
+            const int o = in ? am * bw + xs + an : 0;
+            mk[t] = in ? stage[moff + o] : 1;
+            sv[t] = in ? (float)stage[o] : 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < NPOS; ++t) {
+            const int pix = lt + t * TB;
+            const int yy = min(max(blk.y - d + pix / F - off, 0), P.H - 1);
+            const int xx = min(max(blk.x - d + pix % F - off, 0), P.W - 1);
+            mk[t] = P.mask[((size_t)blk.image * P.H + yy) * P.W + xx];
+            const char *row = static_cast<const char *>(P.images) + ((long long)blk.image * P.H + yy) * P.pitch;
+            sv[t] = P.dtype == 0 ? (float)reinterpret_cast<const uint8_t *>(row)[xx]
+                                 : reinterpret_cast<const float *>(row)[xx];
+        }
     }
     float smax = 0.f;
 #pragma unroll
@@ -1037,13 +1126,14 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
 
 template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false>
 __device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
-                                              unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
+                                              unsigned char *smem, const float2 *s_tw, RedShared *rsh,
+                                              uint32_t &tph) {
     constexpr int TB = Geo<F, PAIRS, FT>::TB;
     if constexpr (FT == 1) {
         constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
         constexpr int NPL = PAIRS / 2;                // covers b <= F/2
-        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT>(P, C, first, count, smem, s_tw, rsh);
-        else process<F, PAIRS, NT, NPL, EXT>(P, C, first, count, smem, s_tw, rsh);
+        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT>(P, C, first, count, smem, s_tw, rsh, tph);
+        else process<F, PAIRS, NT, NPL, EXT>(P, C, first, count, smem, s_tw, rsh, tph);
     } else {
         // a volume's block group is FT times larger: b <= F/2 needs
         // F^2/4 / TB = PAIRS / (2 FT) samples per thread (at least 1)
@@ -1069,6 +1159,8 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
     __shared__ int s_item;
     __shared__ RedShared rsh;
     for (int i = threadIdx.x; i < 64; i += NT) s_tw[i] = P.tw[i];
+    if (threadIdx.x == 0 && P.tma) mbar_init(&rsh.mbar, 1);
+    uint32_t tph = 0;   // phase of rsh.mbar the next window waits for
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.counter, 1);
@@ -1083,16 +1175,16 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
         const int count = min(C.bpi, P.seg_block_start[sg] + P.seg_block_count[sg] - first);
         if (EXT && C.FT == 4) {
             if constexpr (EXT) {
-                if (C.F == 32) process_class<32, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh);
-                else process_class<16, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh);
+                if (C.F == 32) process_class<32, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh, tph);
+                else process_class<16, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh, tph);
             }
         } else if constexpr (KS == kSetF64) {
-            process_class<64, PAIRS, NT, 1, false>(P, C, first, count, smem, s_tw, &rsh);
+            process_class<64, PAIRS, NT, 1, false>(P, C, first, count, smem, s_tw, &rsh, tph);
         } else {
             switch (C.F) {
-                case 64: process_class<64, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
-                case 32: process_class<32, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
-                default: process_class<16, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh); break;
+                case 64: process_class<64, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                case 32: process_class<32, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                default: process_class<16, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh, tph); break;
             }
         }
         __syncthreads();
