@@ -4,17 +4,21 @@ Readings used (also in the design notes):
   - selections are compared modulo the global conjugate mirror
     (u, v) -> (-u, -v) mod F: for real input the two choices give the same
     Re{g} (the mirrored trajectory has R' = conj(R[-k]) and g' = conj(g));
-  - every GPU pick must be an epsilon-argmax of the oracle's FP64 residual
-    along the same selection sequence: |R_w[pick]|^2 >= (1 - eps) max |R_w|^2
-    with eps = EPS_TIE + ROUND_K * delta, where delta = |e32 - e64| / e64 is
-    the relative deviation of the kernel's own FP32 energy of that pick from
-    its FP64 value.  The argmax is decided in the kernel's precision: late in
-    the iteration, when the residual has fallen far below the initial
-    spectrum, FP32 cannot order energies closer than a few delta, and such a
-    pick is a tie at that precision.  delta itself must stay below
-    DELTA_MAX, so a wrong residual cannot hide behind a widened band;
+  - every GPU pick must be a near-tie argmax of the oracle's FP64 residual
+    along the same selection sequence (guided replay): |R_w[pick]|^2 >=
+    (1 - EPS_TIE) max |R_w|^2 with EPS_TIE = 1e-5, the near-tie band of the
+    top-two energies.  A pick that is not the FP64 argmax is then one of
+    near-tied maxima, so the selection sequence differs from the oracle's
+    only at near-ties.  The kernel's own FP32 energy of each pick must lie
+    within DELTA_MAX (relative) of its FP64 value;
   - pixels are compared with the oracle replayed along the GPU's selection
     sequence (guided replay), |GPU - oracle| <= PIX_TOL on the 0-255 scale.
+
+Every block also reports the picks outside EPS_TIE (the bar above fails
+on any), how far the widened band EPS_TIE + ROUND_K * delta would have
+reached, and, for blocks whose selections left the free-running oracle's at
+a near-tie, the pixel difference against the free-running oracle.
+summarize() totals them and the tests bound how often blocks diverge.
 """
 from __future__ import annotations
 
@@ -27,7 +31,7 @@ import oracle
 from oracle import image as oimage
 
 EPS_TIE = 1e-5      # near-tie band of the top-two energies (relative)
-ROUND_K = 4.0       # band widening per unit of measured FP32 energy deviation
+ROUND_K = 4.0       # reported only: how far a delta-widened band would reach
 DELTA_MAX = 2e-4    # largest FP32 energy deviation accepted at any pick
 PIX_TOL = 1e-2      # absolute pixel tolerance, 0-255 scale
 
@@ -56,10 +60,12 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
         s_grid = np.where(w_grid > 0, s_grid - e_grid, 0.0)
         est_b = est[k["border"]:k["border"] + b, k["border"]:k["border"] + b]
     out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False,
-               max_delta=0.0, widened=False)
+               max_delta=0.0, widened=False, picks=0, wide_picks=0, wide_gap=0.0, wide_delta=0.0,
+               free_pix=0.0)
     free = oracle.cfse(s_grid, w_grid, k["gamma"], I)
     r0 = off + k["border"]
     free_patch = free.g.real[r0:r0 + b, r0:r0 + b] + est_b
+    out["free_pix"] = float(np.max(np.abs(free_patch - gpu_patch))) if b else 0.0
     if gpu_sel is None:
         # no trace: only the free run can be compared
         out["max_pix"] = float(np.max(np.abs(free_patch - gpu_patch)))
@@ -90,10 +96,15 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
         else:
             delta = np.zeros(I)
         out["max_delta"] = float(delta.max())
-        band = EPS_TIE + ROUND_K * delta
-        if np.any(1.0 - ratio > band) or out["max_delta"] > DELTA_MAX:
+        if np.any(1.0 - ratio > EPS_TIE) or out["max_delta"] > DELTA_MAX:
             out["ok"] = False
-        out["widened"] = bool(np.any(1.0 - ratio > EPS_TIE))
+        wide = 1.0 - ratio > EPS_TIE
+        out["widened"] = bool(np.any(wide))
+        out["picks"] = int(I)
+        out["wide_picks"] = int(np.count_nonzero(wide))
+        if out["widened"]:
+            out["wide_gap"] = float(np.max((1.0 - ratio)[wide]))
+            out["wide_delta"] = float(np.max(delta[wide]))
     gp = guided.g.real[r0:r0 + b, r0:r0 + b] + est_b
     out["max_pix"] = float(np.max(np.abs(gp - gpu_patch)))
     if out["max_pix"] > PIX_TOL:
@@ -115,7 +126,8 @@ def check_block3(video, mask, blk, cls, gpu_patch, gpu_sel, gpu_energy):
     F, Ft, b, I = k["fft"], 4, k["block"], k["iters"]
     kk = dict(k, fft_t=Ft)
     s, w, toff, off = oimage.area_inputs3(video, mask, t0, x, y, b, k["border"], F, Ft, k["frames"], k["rho"])
-    out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False, max_delta=0.0, widened=False)
+    out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False, max_delta=0.0, widened=False,
+               picks=0, wide_picks=0, wide_gap=0.0, wide_delta=0.0, free_pix=0.0)
     free = oracle.cfse3(s, w, k["gamma"], I)
     gsel = np.asarray(gpu_sel[:I], dtype=np.int64)
     if I:
@@ -136,11 +148,18 @@ def check_block3(video, mask, blk, cls, gpu_patch, gpu_sel, gpu_energy):
         delta = np.abs(e32 - guided.e_sel) / np.maximum(guided.e_sel, 1e-300)
         delta[guided.e_sel == 0] = 0.0
         out["max_delta"] = float(delta.max())
-        if np.any(1.0 - ratio > EPS_TIE + ROUND_K * delta) or out["max_delta"] > DELTA_MAX:
+        if np.any(1.0 - ratio > EPS_TIE) or out["max_delta"] > DELTA_MAX:
             out["ok"] = False
-        out["widened"] = bool(np.any(1.0 - ratio > EPS_TIE))
+        wide = 1.0 - ratio > EPS_TIE
+        out["widened"] = bool(np.any(wide))
+        out["picks"] = int(I)
+        out["wide_picks"] = int(np.count_nonzero(wide))
+        if out["widened"]:
+            out["wide_gap"] = float(np.max((1.0 - ratio)[wide]))
+            out["wide_delta"] = float(np.max(delta[wide]))
     tc = toff + (k["frames"] - 1) // 2
     r0 = off + k["border"]
+    out["free_pix"] = float(np.max(np.abs(free.g.real[tc, r0:r0 + b, r0:r0 + b] - gpu_patch)))
     gp = guided.g.real[tc, r0:r0 + b, r0:r0 + b]
     out["max_pix"] = float(np.max(np.abs(gp - gpu_patch)))
     if out["max_pix"] > PIX_TOL:
@@ -181,5 +200,32 @@ def summarize(results):
     n_mir = sum(r["mirror"] for r in results)
     n_wid = sum(r["widened"] for r in results)
     max_delta = max((r["max_delta"] for r in results), default=0.0)
+    picks = sum(r.get("picks", 0) for r in results)
+    wide_picks = sum(r.get("wide_picks", 0) for r in results)
+    div = [r for r in results if r["first_div"] is not None]
     return dict(ok=ok, n=len(results), worst_pix=worst_pix, worst_ratio=worst_ratio,
-                diverged=n_div, mirrored=n_mir, widened=n_wid, max_delta=max_delta)
+                diverged=n_div, mirrored=n_mir, widened=n_wid, max_delta=max_delta,
+                picks=picks, wide_picks=wide_picks, wide_frac=wide_picks / max(picks, 1),
+                wide_gap=max((r.get("wide_gap", 0.0) for r in results), default=0.0),
+                wide_delta=max((r.get("wide_delta", 0.0) for r in results), default=0.0),
+                div_frac=n_div / max(len(results), 1),
+                div_first=min((r["first_div"] for r in div), default=None),
+                div_free_pix=max((r.get("free_pix", 0.0) for r in div), default=0.0))
+
+
+# Bounds per batch: picks outside the near-tie band (none: the check above
+# already fails on one), and blocks whose selection sequence leaves the
+# free-running oracle's at a near-tie.  Measured on the GB300 with every GPU
+# test: 0.4-2.1% of the blocks of the plain batches (256 to 1121 blocks),
+# 9.4% and 13.5% of the warm-start batches (noisy estimates leave more
+# near-tied residual bins); the bound is 20%.
+MAX_WIDE_FRAC = 0.0      # of all picks of a batch
+MAX_DIV_FRAC = 0.2       # of the blocks of a batch (with at least 20 blocks)
+
+
+def assert_strict_bounds(s, min_blocks=20):
+    """The strict-band bounds on a summarize() result (batches of at least
+    min_blocks blocks for the divergence bound)."""
+    assert s["wide_frac"] <= MAX_WIDE_FRAC, s
+    if s["n"] >= min_blocks:
+        assert s["div_frac"] <= MAX_DIV_FRAC, s

@@ -5,7 +5,15 @@ The oracle evaluates the same bf16-rounded weights, inputs and stored
 activations in FP64; the GPU accumulates in FP32 in a different order, so a
 stored activation can land on the other side of a bf16 rounding boundary.
 Tolerances: forward, every output within 2^-6 of the output RMS and 99.9%
-within 2^-9; gradients, relative L2 error <= 1e-2 per layer.
+within 2^-9.  Gradients, element by element: |g - g_ref| <= GRAD_ATOL x the
+RMS of the layer's reference weight (or bias) gradient + GRAD_RTOL x |g_ref|.
+A gradient element sums, over every output position, products of a stored
+bf16 activation (relative rounding 2^-9) and a back-propagated FP32 error
+that itself carries the forward's bf16 differences; an element near zero is
+a difference of such sums, hence the absolute part scaled by the layer's
+RMS.  A stored activation that rounds the other way moves one term of such
+a sum by at most 2^-8 of that term; the bounds are 2^-10 of the RMS plus
+2^-10 relative (measured on the GB300: at most 1.5e-5 of the RMS).
 """
 import numpy as np
 import pytest
@@ -22,6 +30,10 @@ def P():
         pytest.skip("no CUDA device")
     import paper_2204_14193_gb300 as P
     return P
+
+
+GRAD_ATOL = 2.0 ** -10   # x the layer's reference gradient RMS
+GRAD_RTOL = 2.0 ** -10   # x |g_ref|
 
 
 def _inputs(seed, n, H, W):
@@ -63,10 +75,13 @@ def test_gradient_matches_oracle(P):
                             lf.astype(np.float64))
     assert loss == pytest.approx(rl, rel=1e-3)
     for ws, bs, cin, cout, d in ocnn.layer_slices():
-        for sl in (ws, bs):
-            err = np.linalg.norm(g[sl] - rg[sl]) / max(np.linalg.norm(rg[sl]), 1e-30)
-            print("layer", d, "rel err", err)
-            assert err <= 1e-2
+        for name, sl in (("weights", ws), ("biases", bs)):
+            ref, got = rg[sl], g[sl].astype(np.float64)
+            rms = max(np.sqrt(np.mean(ref ** 2)), 1e-30)
+            excess = np.abs(got - ref) / (GRAD_ATOL * rms + GRAD_RTOL * np.abs(ref))
+            print(f"layer dilation {d} {name}: max |d|/rms {np.max(np.abs(got - ref)) / rms:.2e}, "
+                  f"worst element at {excess.max():.3f} of the bound")
+            assert np.all(excess <= 1.0), (d, name, int(np.argmax(excess)), excess.max())
 
 
 def test_adam_step_matches_oracle(P):

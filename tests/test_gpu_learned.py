@@ -56,6 +56,7 @@ def test_warm_start_parity_f64(P):
     s = parity.summarize(parity.check_batch(img, mask, blocks, [C64], patches, sel, energy, ests=est))
     print("warm start parity:", s)
     assert s["ok"], s
+    parity.assert_strict_bounds(s)
     for i, (_, x, y, _c) in enumerate(blocks[:8]):
         np.testing.assert_array_equal(out[0, y:y + 16, x:x + 16].ravel(), patches[256 * i:256 * (i + 1)])
 
@@ -71,6 +72,7 @@ def test_warm_start_parity_uneven(P):
     s = parity.summarize(parity.check_batch(img, mask, blocks, cls, patches, sel, energy, ests=est))
     print("warm start parity (uneven):", s)
     assert s["ok"], s
+    parity.assert_strict_bounds(s)
 
 
 def _learned_scene():

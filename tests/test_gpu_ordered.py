@@ -54,7 +54,7 @@ def test_ordered_matches_oracle(P, cls, b):
     for j, (patch, r) in enumerate(res):
         ratio = r.e_sel / np.maximum(r.e_max, 1e-300)
         delta = np.abs(energy[j, :I] - r.e_sel) / np.maximum(r.e_sel, 1e-300)
-        assert np.all(1.0 - ratio <= parity.EPS_TIE + parity.ROUND_K * delta), j
+        assert np.all(1.0 - ratio <= parity.EPS_TIE), j
         assert delta.max() <= parity.DELTA_MAX, (j, delta.max())
         got = patches[j * b * b:(j + 1) * b * b].reshape(b, b)
         worst_pix = max(worst_pix, float(np.abs(got - patch).max()))

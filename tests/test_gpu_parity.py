@@ -49,6 +49,7 @@ def assert_parity(images, mask, blocks, classes, patches, trace):
     s = parity.summarize(res)
     print("parity:", s)
     assert s["ok"], s
+    parity.assert_strict_bounds(s)
     return s
 
 
@@ -241,6 +242,7 @@ def test_full_size_throughput_config_sampled(fse):
     s = parity.summarize(out)
     print("full-size sample:", s)
     assert s["ok"], s
+    parity.assert_strict_bounds(s)
 
 
 def test_full_size_uneven_config_sampled(fse):
@@ -281,6 +283,7 @@ def test_full_size_uneven_config_sampled(fse):
     s = parity.summarize(out)
     print("uneven full-size sample:", s)
     assert s["ok"], s
+    parity.assert_strict_bounds(s)
 
 
 # ------------------------------------------------- model over the whole area

@@ -51,6 +51,7 @@ def _check(video, mask, blocks, classes, patches, sel, energy):
     s = parity.summarize(res)
     print("video parity:", s)
     assert s["ok"], s
+    parity.assert_strict_bounds(s)
 
 
 def test_video_volume_parity(P):
