@@ -67,8 +67,14 @@ typedef enum {
  * initialisation, the `out`
  * image of fse_extrapolate_batch required (the concealed values are read
  * from it); not with the host-buffer or allocation-free entry points.  On
- * the GPU a block waits (bounded, 1 s) for the blocks it reuses. */
+ * the GPU a block waits (bounded by the handle's wait limit, see
+ * fse_set_wait_limit) for the blocks it reuses. */
 #define FSE_FLAG_ORDERED 2u
+/* Outputs as 8-bit sample values: every concealed sample is clamped to
+ * [0, 255] and rounded to the nearest integer, ties to even (still written
+ * as FP32).  Without it the output is the unclamped model Re{g} (Algorithm 1
+ * produces real values; the paper does not round). */
+#define FSE_FLAG_CLAMP_U8 4u
 
 /*
  * One block-size class.
@@ -143,7 +149,10 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg);
  * buffers.
  *   images       device, dtype FSE_DTYPE_U8 or FSE_DTYPE_F32, geometry above
  *   loss_mask    device, uint8, 1 = lost sample, geometry above
- *   blocks       HOST array of n_blocks descriptors (read during the call)
+ *   blocks       n_blocks descriptors in host memory (read during the call)
+ *                or in device memory of the handle's device (copied to the
+ *                host on cuda_stream first, after the stream's earlier work:
+ *                the call then waits for the stream)
  *   out          device FP32 image (geometry above) or NULL; only B samples
  *                of each block are written
  *   patches      device FP32 array or NULL: block i's b x b result (row-major)
@@ -222,6 +231,15 @@ fse_status fse_extrapolate_batch_host(fse_handle *h, const void *images, int dty
 fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef,
                          size_t cap, int *stride_out);
 
+/* The top-two gap of every selection of the last batch (FSE_FLAG_TRACE
+ * only), in the layout of fse_get_trace: (e1 - e2) / e1, e1 the selected
+ * bin's FP32 energy |R_w[u,v]|^2 and e2 the largest FP32 energy of the other
+ * bins at that selection (0 where e1 = 0).  It tells how close each pick was
+ * to a tie in the kernel's own precision: Section III selects the maximum,
+ * and a pick whose gap is below the arithmetic's resolution could have gone
+ * to the runner-up.  cap as fse_get_trace.  Synchronises the last stream. */
+fse_status fse_get_trace_gap(fse_handle *h, float *gap2, size_t cap);
+
 /* The model over every lost block's whole extrapolation area, for the last
  * batch of a handle created with FSE_FLAG_TRACE: Re{g}[m][n] for the M x M
  * area, the inverse transform of the accumulated model spectrum G of
@@ -234,12 +252,27 @@ fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef
  * Errors: FSE_ERR_INVALID_ARG (no trace flag, NULL model, short stride). */
 fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, void *cuda_stream);
 
-/* Wait for the handle's last launch and report device-side failures: the
- * learned-initialisation kernel bounds every wait on its tensor-core work
- * (1 s) and, when one expires, records it, frees its tensor memory and
- * stops; fse_sync then returns FSE_ERR_TIMEOUT (and clears the record).
- * No counterpart in the paper. */
+/* Wait for the handle's last launch and report what the kernels recorded on
+ * the device (no counterpart in the paper), then clear the record:
+ *   FSE_ERR_TIMEOUT      a bounded device wait ran out: the TMA gather of a
+ *                        window, an ordered block's wait for the blocks it
+ *                        reuses, or the learned-initialisation network's wait
+ *                        for its tensor-core work.  The kernel records it,
+ *                        waits at most 1 s more for its own copies or MMAs in
+ *                        flight, frees its tensor memory and carries on or
+ *                        stops; the outputs of that launch are not valid.
+ *   FSE_ERR_INVALID_ARG  a block's loss area B is not marked lost in the
+ *                        loss mask (the blocks must be lost samples); that
+ *                        block was concealed as if B were lost.
+ * The handle stays usable after either. */
 fse_status fse_sync(fse_handle *h);
+
+/* Limit of every bounded device wait of the handle's launches, in
+ * nanoseconds of the GPU's global timer (default 1e9 = 1 s, at most 60 s).
+ * 0 lets a wait expire as soon as its first poll fails, which tests use to
+ * exercise the timeout path.  Takes effect from the next call (a captured
+ * launch is re-captured).  No counterpart in the paper. */
+fse_status fse_set_wait_limit(fse_handle *h, unsigned long long ns);
 
 /* ------------------------------------------------------------------------
  * Learned initialisation network (no counterpart in the paper).
@@ -269,6 +302,15 @@ fse_status fse_cnn_create(fse_cnn **out, int device, int height, int width, int 
  * and step count) or out.  Synchronous. */
 fse_status fse_cnn_set_params(fse_cnn *c, const float *params, size_t n);
 fse_status fse_cnn_get_params(fse_cnn *c, float *params, size_t n);
+
+/* The whole training state, for checkpoints: the FP32 master parameters,
+ * Adam's first and second moments (FSE_CNN_PARAMS host FP32 values each)
+ * and the number of Adam steps taken (which sets the bias corrections).
+ * Setting it and training on continues bit for bit where the state was
+ * taken (the gradients are reduced in a fixed order).  Synchronous. */
+fse_status fse_cnn_get_state(fse_cnn *c, float *params, float *m, float *v, long long *step);
+fse_status fse_cnn_set_state(fse_cnn *c, const float *params, const float *m, const float *v,
+                             long long step);
 
 /* Inference on n areas: x device [n][2][H][W] FP32, y device [n][H][W] FP32.
  * Asynchronous on cuda_stream. */
@@ -338,6 +380,15 @@ fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, int n_classes
  * register pair from shared memory, are reported against.  Synchronous;
  * allocates a few bytes of device memory.  Errors: fse_last_error(NULL). */
 fse_status fse_measure_smem_bandwidth(int device, double *gbytes_per_s);
+
+/* Test hooks for fault injection (no counterpart in the paper).
+ * fse_test_fail_allocation(n): the n-th device or pinned-host allocation the
+ * library makes from now on fails as if memory were exhausted (the call that
+ * made it returns FSE_ERR_OOM); n = 0 disarms.  Process-wide.
+ * fse_test_live_allocations(): device and pinned-host allocations the
+ * library holds now (handles, networks, staging), to check for leaks. */
+void fse_test_fail_allocation(int n);
+long long fse_test_live_allocations(void);
 
 /* Reason for the last failure on h (or, when h is NULL, of fse_create or
  * fse_extrapolate_batch_noalloc); never NULL; valid until the next call. */

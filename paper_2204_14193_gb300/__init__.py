@@ -27,6 +27,7 @@ FSE_DTYPE_U8, FSE_DTYPE_F32 = 0, 1
 FSE_INIT_ZERO, FSE_INIT_LEARNED = 0, 1
 FSE_FLAG_TRACE = 1
 FSE_FLAG_ORDERED = 2
+FSE_FLAG_CLAMP_U8 = 4
 STATUS = {0: "FSE_OK", 1: "FSE_ERR_INVALID_ARG", 2: "FSE_ERR_UNSUPPORTED", 3: "FSE_ERR_CUDA",
           4: "FSE_ERR_OOM", 5: "FSE_ERR_TIMEOUT", 6: "FSE_ERR_NOT_TRAINED"}
 
@@ -80,9 +81,15 @@ def _load():
             lib.fse_load_init_weights.argtypes = [vp, vp, sz]
             lib.fse_get_area_model.argtypes = [vp, vp, sz, vp]
             lib.fse_sync.argtypes = [vp]
+            lib.fse_set_wait_limit.argtypes = [vp, ctypes.c_ulonglong]
             lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
                                                           c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
+            lib.fse_get_trace_gap.argtypes = [vp, vp, sz]
+            lib.fse_test_fail_allocation.argtypes = [c_int]
+            lib.fse_test_fail_allocation.restype = None
+            lib.fse_test_live_allocations.argtypes = []
+            lib.fse_test_live_allocations.restype = ctypes.c_longlong
             lib.fse_measure_smem_bandwidth.argtypes = [c_int, ctypes.POINTER(ctypes.c_double)]
             lib.fse_measure_smem_bandwidth.restype = c_int
             lib.fse_last_error.argtypes = [vp]
@@ -91,7 +98,8 @@ def _load():
             lib.fse_destroy.restype = None
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
                       "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_extrapolate_batch_init",
-                      "fse_load_init_weights", "fse_get_area_model", "fse_sync"):
+                      "fse_load_init_weights", "fse_get_area_model", "fse_sync", "fse_set_wait_limit",
+                      "fse_get_trace_gap"):
                 getattr(lib, n).restype = c_int
             fp = ctypes.POINTER(ctypes.c_float)
             lib.fse_cnn_param_count.restype = sz
@@ -99,6 +107,8 @@ def _load():
             lib.fse_cnn_set_params.argtypes = [vp, vp, sz]
             lib.fse_cnn_get_params.argtypes = [vp, vp, sz]
             lib.fse_cnn_forward.argtypes = [vp, vp, c_int, vp, vp]
+            lib.fse_cnn_get_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_longlong)]
+            lib.fse_cnn_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_longlong]
             lib.fse_cnn_loss_grad.argtypes = [vp, vp, vp, vp, c_int, vp, fp, vp]
             lib.fse_cnn_train_step.argtypes = [vp, vp, vp, vp, c_int, ctypes.c_float, fp, vp]
             lib.fse_cnn_last_error.argtypes = [vp]
@@ -106,7 +116,7 @@ def _load():
             lib.fse_cnn_destroy.argtypes = [vp]
             lib.fse_cnn_destroy.restype = None
             for n in ("fse_cnn_create", "fse_cnn_set_params", "fse_cnn_get_params", "fse_cnn_forward",
-                      "fse_cnn_loss_grad", "fse_cnn_train_step"):
+                      "fse_cnn_loss_grad", "fse_cnn_train_step", "fse_cnn_get_state", "fse_cnn_set_state"):
                 getattr(lib, n).restype = c_int
             _lib = lib
     return _lib
@@ -133,11 +143,15 @@ def fse_create(cfg: fse_config):
 def fse_extrapolate_batch(h, images: int, dtype: int, n_images: int, height: int, width: int,
                           pitch_bytes: int, loss_mask: int, blocks: np.ndarray, n_blocks: int,
                           out: int | None, patches: int | None, stream: int | None) -> None:
-    """Device-pointer entry point; ``blocks`` is a host int32 [n, 4] array."""
-    blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+    """Device-pointer entry point; ``blocks`` is a host int32 [n, 4] array or
+    the address (int) of such an array in device memory."""
+    if isinstance(blocks, int):
+        bptr = blocks if n_blocks else None
+    else:
+        blocks = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, 4)
+        bptr = blocks.ctypes.data if n_blocks else None
     st = _load().fse_extrapolate_batch(h, images, dtype, n_images, height, width, pitch_bytes,
-                                       loss_mask, blocks.ctypes.data if n_blocks else None, n_blocks,
-                                       out, patches, stream)
+                                       loss_mask, bptr, n_blocks, out, patches, stream)
     _check(st, h)
 
 
@@ -204,12 +218,27 @@ def fse_get_trace(h, n_blocks: int):
             (co[0:2 * n:2] + 1j * co[1:2 * n:2]).astype(np.complex64).reshape(n_blocks, s))
 
 
+def fse_get_trace_gap(h, n_blocks: int) -> np.ndarray:
+    """Top-two gap (e1 - e2) / e1 of every selection, float32 [n, stride]."""
+    stride = ctypes.c_int(0)
+    lib = _load()
+    _check(lib.fse_get_trace(h, None, None, None, 0, ctypes.byref(stride)), h)
+    n = n_blocks * stride.value
+    gap = np.zeros(max(n, 1), np.float32)
+    _check(lib.fse_get_trace_gap(h, gap.ctypes.data, max(n, 1)), h)
+    return gap[:n].reshape(n_blocks, stride.value)
+
+
 def fse_get_area_model(h, model: int, model_stride: int, stream: int | None) -> None:
     _check(_load().fse_get_area_model(h, model, model_stride, stream), h)
 
 
 def fse_sync(h) -> None:
     _check(_load().fse_sync(h), h)
+
+
+def fse_set_wait_limit(h, ns: int) -> None:
+    _check(_load().fse_set_wait_limit(h, int(ns)), h)
 
 
 def fse_measure_smem_bandwidth(device: int = 0) -> float:
@@ -250,6 +279,19 @@ def fse_cnn_get_params(c) -> np.ndarray:
     return out
 
 
+def fse_cnn_get_state(c):
+    """(params, m, v, step): the network's full training state."""
+    p, m, v = (np.zeros(FSE_CNN_PARAMS, np.float32) for _ in range(3))
+    step = ctypes.c_longlong(0)
+    _cnn_check(_load().fse_cnn_get_state(c, p.ctypes.data, m.ctypes.data, v.ctypes.data, ctypes.byref(step)), c)
+    return p, m, v, int(step.value)
+
+
+def fse_cnn_set_state(c, params, m, v, step: int) -> None:
+    p, m, v = (np.ascontiguousarray(a, dtype=np.float32) for a in (params, m, v))
+    _cnn_check(_load().fse_cnn_set_state(c, p.ctypes.data, m.ctypes.data, v.ctypes.data, int(step)), c)
+
+
 def fse_cnn_forward(c, x: int, n: int, y: int, stream: int | None) -> None:
     _cnn_check(_load().fse_cnn_forward(c, x, n, y, stream), c)
 
@@ -287,6 +329,13 @@ class Cnn:
 
     def get_params(self):
         return fse_cnn_get_params(self.c)
+
+    def get_state(self):
+        """(params, m, v, step): parameters, Adam moments and step count."""
+        return fse_cnn_get_state(self.c)
+
+    def set_state(self, params, m, v, step):
+        fse_cnn_set_state(self.c, params, m, v, step)
 
     def _stream(self):
         import torch
@@ -332,7 +381,8 @@ def he_init(seed: int) -> np.ndarray:
 
 # --------------------------------------------------------- convenience API
 def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero",
-                init_iters: int = 0, ordered: bool = False, reuse_weight: float = 0.5) -> fse_config:
+                init_iters: int = 0, ordered: bool = False, reuse_weight: float = 0.5,
+                clamp_u8: bool = False) -> fse_config:
     cfg = fse_config()
     cfg.n_classes = len(classes)
     for i, c in enumerate(classes):
@@ -341,7 +391,8 @@ def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero
     cfg.init = FSE_INIT_LEARNED if init == "learned" else FSE_INIT_ZERO
     cfg.init_iters = int(init_iters)
     cfg.device = device
-    cfg.flags = (FSE_FLAG_TRACE if trace else 0) | (FSE_FLAG_ORDERED if ordered else 0)
+    cfg.flags = ((FSE_FLAG_TRACE if trace else 0) | (FSE_FLAG_ORDERED if ordered else 0)
+                 | (FSE_FLAG_CLAMP_U8 if clamp_u8 else 0))
     cfg.reuse_weight = float(reuse_weight)
     return cfg
 
@@ -353,9 +404,10 @@ class Engine:
     """
 
     def __init__(self, classes, device: int = 0, trace: bool = False, init: str = "zero", init_iters: int = 0,
-                 weights=None, ordered: bool = False, reuse_weight: float = 0.5):
+                 weights=None, ordered: bool = False, reuse_weight: float = 0.5, clamp_u8: bool = False):
         self.classes = [dict(c) for c in classes]
-        self.h = fse_create(make_config(classes, device, trace, init, init_iters, ordered, reuse_weight))
+        self.h = fse_create(make_config(classes, device, trace, init, init_iters, ordered, reuse_weight,
+                                        clamp_u8))
         self.last_n = 0
         if weights is not None:
             fse_load_init_weights(self.h, weights)
@@ -425,10 +477,19 @@ class Engine:
     def trace(self):
         return fse_get_trace(self.h, self.last_n)
 
+    def trace_gap(self):
+        """Top-two gap of every selection of the last batch (trace handles)."""
+        return fse_get_trace_gap(self.h, self.last_n)
+
     def sync(self):
         """Wait for the last launch; raises FseError(FSE_ERR_TIMEOUT) when a
-        bounded device-side wait expired."""
+        bounded device-side wait expired, FseError(FSE_ERR_INVALID_ARG) when a
+        block's loss area was not marked lost in the mask."""
         fse_sync(self.h)
+
+    def set_wait_limit(self, ns: int):
+        """Limit of the bounded device waits in nanoseconds (default 1 s)."""
+        fse_set_wait_limit(self.h, ns)
 
     def area_model(self, stream=None):
         """Re{g} over every block's M x M area of the last batch (trace

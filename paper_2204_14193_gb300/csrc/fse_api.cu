@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "fse.h"
+#include "fse_alloc.cuh"
 #include "fse_cnn.cuh"
 #include "fse_cnn_tc.cuh"
 #include "fse_device.cuh"
@@ -97,6 +98,7 @@ struct fse_handle {
     int *d_tr_sel = nullptr;
     float *d_tr_energy = nullptr;
     float2 *d_tr_coef = nullptr;
+    float *d_tr_second = nullptr;   // largest energy besides the pick, per selection
     size_t tr_cap = 0;
     int tr_stride = 0;
     int last_n_blocks = 0;
@@ -133,7 +135,8 @@ struct fse_handle {
     int learned_n = 0;
     uint8_t *d_tc_w = nullptr;      // tensor-core network: packed B operands
     bool tc_net = false;            // 16x16 blocks with a 16-sample border: tcgen05 kernel
-    int *d_err = nullptr;           // device-side error status (bounded waits)
+    int *d_err = nullptr;           // device status word (fse::kErr* bits, read by fse_sync)
+    unsigned long long wait_ns = 1000000000ull;   // limit of every bounded device wait
     // ordered concealment (FSE_FLAG_ORDERED): neighbour lists and done flags
     int *d_nb_start = nullptr, *d_nb_list = nullptr, *d_done = nullptr;
     size_t nb_start_cap = 0, nb_list_cap = 0, done_cap = 0;
@@ -150,6 +153,7 @@ struct fse_handle {
     BlockRec *h_cblocks = nullptr;  // pinned staging
     size_t h_cblocks_cap = 0;
     int *d_ccounter = nullptr;
+    std::vector<fse_block> hb_stage;   // host copy of a device-resident block list
     std::string err = "no error";
 };
 
@@ -216,7 +220,7 @@ fse_status validate_config(const fse_config *cfg) {
         if (cfg->init_iters < 0 || cfg->init_iters > 4096)
             return fail(nullptr, FSE_ERR_INVALID_ARG, "init_iters %d not in [0, 4096]", cfg->init_iters);
     }
-    if (cfg->flags & ~(FSE_FLAG_TRACE | FSE_FLAG_ORDERED))
+    if (cfg->flags & ~(FSE_FLAG_TRACE | FSE_FLAG_ORDERED | FSE_FLAG_CLAMP_U8))
         return fail(nullptr, FSE_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
     if (cfg->flags & FSE_FLAG_ORDERED) {
         // fft 16 is excluded: its blocks share warps, and a lane waiting for an
@@ -342,7 +346,8 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         const fse_class &k = cfg.cls[pl.seg_cls[sg]];
         all_f64 = all_f64 && k.fft == 64 && k.frames <= 1;
     }
-    pl.ks = fse::kernel_set_for(h->ext, all_f64);
+    // traced batches record the top-two gap, which the FFT-64 set leaves out
+    pl.ks = fse::kernel_set_for(h->ext, all_f64 && !(cfg.flags & FSE_FLAG_TRACE));
     return FSE_OK;
 }
 
@@ -431,10 +436,10 @@ template <typename T>
 fse_status grow(fse_handle *h, T **ptr, size_t *cap, size_t need) {
     if (need <= *cap) return FSE_OK;
     const size_t n = std::max(need, *cap + *cap / 2);
-    if (*ptr) cudaFree(*ptr);
+    if (*ptr) fse::dev_free(*ptr);
     *ptr = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(ptr), n * sizeof(T));
+    cudaError_t e = fse::dev_malloc(reinterpret_cast<void **>(ptr), n * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
     *cap = n;
     return FSE_OK;
@@ -707,10 +712,10 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     // upload the sorted block list through pinned staging
     if (h->upload_done) cudaEventSynchronize(h->upload_done);
     if ((size_t)n_blocks > h->h_blocks_cap) {
-        if (h->h_blocks) cudaFreeHost(h->h_blocks);
+        if (h->h_blocks) fse::host_free(h->h_blocks);
         h->h_blocks = nullptr;
         h->h_blocks_cap = 0;
-        FSE_CUDA(h, cudaMallocHost(&h->h_blocks, (size_t)n_blocks * sizeof(BlockRec)));
+        FSE_CUDA(h, fse::host_malloc(&h->h_blocks, (size_t)n_blocks * sizeof(BlockRec)));
         h->h_blocks_cap = n_blocks;
     }
     st = grow(h, &h->d_blocks, &h->blocks_cap, (size_t)n_blocks);
@@ -722,16 +727,19 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     if (trace) {
         const size_t need = (size_t)n_blocks * stride;
         if (need > h->tr_cap) {
-            cudaFree(h->d_tr_sel);
-            cudaFree(h->d_tr_energy);
-            cudaFree(h->d_tr_coef);
+            fse::dev_free(h->d_tr_sel);
+            fse::dev_free(h->d_tr_energy);
+            fse::dev_free(h->d_tr_coef);
+            fse::dev_free(h->d_tr_second);
             h->d_tr_sel = nullptr;
             h->d_tr_energy = nullptr;
             h->d_tr_coef = nullptr;
+            h->d_tr_second = nullptr;
             h->tr_cap = 0;
-            FSE_CUDA(h, cudaMalloc(&h->d_tr_sel, need * sizeof(int)));
-            FSE_CUDA(h, cudaMalloc(&h->d_tr_energy, need * sizeof(float)));
-            FSE_CUDA(h, cudaMalloc(&h->d_tr_coef, need * sizeof(float2)));
+            FSE_CUDA(h, fse::dev_malloc(&h->d_tr_sel, need * sizeof(int)));
+            FSE_CUDA(h, fse::dev_malloc(&h->d_tr_energy, need * sizeof(float)));
+            FSE_CUDA(h, fse::dev_malloc(&h->d_tr_coef, need * sizeof(float2)));
+            FSE_CUDA(h, fse::dev_malloc(&h->d_tr_second, need * sizeof(float)));
             h->tr_cap = need;
         }
     }
@@ -762,6 +770,7 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     P.tr_sel = trace ? h->d_tr_sel : nullptr;
     P.tr_energy = trace ? h->d_tr_energy : nullptr;
     P.tr_coef = trace ? h->d_tr_coef : nullptr;
+    P.tr_second = trace ? h->d_tr_second : nullptr;
     P.tr_stride = stride;
     P.tw = h->d_tw;
     h->learned_launch = learned;
@@ -773,12 +782,21 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         if (st != FSE_OK) return st;
         // the tensor-core network writes B only: the rest of every estimate stays 0
         if (h->est_cap != old_cap) FSE_CUDA(h, cudaMemset(h->d_est, 0, h->est_cap * sizeof(float)));
-        if (!h->tc_net && !h->d_cnn_x) {
+        if (!h->tc_net && !h->d_cnn_out) {
+            // all four buffers or none: a failure frees the ones already made
             const size_t C = (size_t)h->cnn_chunk;
-            FSE_CUDA(h, cudaMalloc(&h->d_cnn_x, C * MM * 2 * sizeof(__nv_bfloat16)));
-            FSE_CUDA(h, cudaMalloc(&h->d_cnn_a0, C * MM * 32 * sizeof(__nv_bfloat16)));
-            FSE_CUDA(h, cudaMalloc(&h->d_cnn_a1, C * MM * 32 * sizeof(__nv_bfloat16)));
-            FSE_CUDA(h, cudaMalloc(&h->d_cnn_out, C * MM * sizeof(float)));
+            cudaError_t e = fse::dev_malloc(&h->d_cnn_x, C * MM * 2 * sizeof(__nv_bfloat16));
+            if (e == cudaSuccess) e = fse::dev_malloc(&h->d_cnn_a0, C * MM * 32 * sizeof(__nv_bfloat16));
+            if (e == cudaSuccess) e = fse::dev_malloc(&h->d_cnn_a1, C * MM * 32 * sizeof(__nv_bfloat16));
+            if (e == cudaSuccess) e = fse::dev_malloc(&h->d_cnn_out, C * MM * sizeof(float));
+            if (e != cudaSuccess) {
+                for (void **p : {reinterpret_cast<void **>(&h->d_cnn_x), reinterpret_cast<void **>(&h->d_cnn_a0),
+                                 reinterpret_cast<void **>(&h->d_cnn_a1), reinterpret_cast<void **>(&h->d_cnn_out)}) {
+                    fse::dev_free(*p);
+                    *p = nullptr;
+                }
+                return cuda_fail(h, e, "network buffers");
+            }
         }
         P.est = h->d_est;
         P.est_stride = MM;
@@ -787,6 +805,8 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         P.est_stride = est_stride;
     }
     P.err = h->d_err;
+    P.wait_ns = h->wait_ns;
+    P.clamp_u8 = (h->cfg.flags & FSE_FLAG_CLAMP_U8) ? 1 : 0;
     P.ordered = ordered ? 1 : 0;
     if (ordered) {
         std::vector<int> nb_start, nb_list;
@@ -839,15 +859,16 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
                             size_t pitch, const uint8_t *loss_mask, const fse_block *blocks, int n_blocks,
                             float *patches, cudaStream_t stream) {
     if (!h->pipe_ready) {
-        FSE_CUDA(h, cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking));
-        FSE_CUDA(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
-        FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming));
-        FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+        // each resource made once (a call that failed half-way resumes here)
+        if (!h->h2d_stream) FSE_CUDA(h, cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking));
+        if (!h->d2h_stream) FSE_CUDA(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
+        if (!h->ev_start) FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming));
+        if (!h->ev_out) FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
         for (int c = 0; c < kHostChunks; ++c) {
-            FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming));
-            FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_k[c], cudaEventDisableTiming));
+            if (!h->ev_in[c]) FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_in[c], cudaEventDisableTiming));
+            if (!h->ev_k[c]) FSE_CUDA(h, cudaEventCreateWithFlags(&h->ev_k[c], cudaEventDisableTiming));
         }
-        FSE_CUDA(h, cudaMalloc(&h->d_ccounter, kHostChunks * sizeof(int)));
+        if (!h->d_ccounter) FSE_CUDA(h, fse::dev_malloc(&h->d_ccounter, kHostChunks * sizeof(int)));
         h->pipe_ready = true;
     }
     const int K = std::min(kHostChunks, std::min(n_images, n_blocks));
@@ -883,15 +904,29 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
     fse_status st = grow(h, &h->d_cblocks, &h->cblocks_cap, (size_t)n_blocks);
     if (st != FSE_OK) return st;
     if ((size_t)n_blocks > h->h_cblocks_cap) {
-        if (h->h_cblocks) cudaFreeHost(h->h_cblocks);
+        if (h->h_cblocks) fse::host_free(h->h_cblocks);
         h->h_cblocks = nullptr;
         h->h_cblocks_cap = 0;
-        FSE_CUDA(h, cudaMallocHost(&h->h_cblocks, (size_t)n_blocks * sizeof(BlockRec)));
+        FSE_CUDA(h, fse::host_malloc(&h->h_cblocks, (size_t)n_blocks * sizeof(BlockRec)));
         h->h_cblocks_cap = n_blocks;
     }
-    FSE_CUDA(h, cudaEventRecord(h->ev_start, stream));
-    FSE_CUDA(h, cudaStreamWaitEvent(h->h2d_stream, h->ev_start, 0));
-    FSE_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, h->ev_start, 0));
+    // from here on, copies and launches may be queued: an error return first
+    // waits for all three streams, so no queued copy still reads or writes
+    // the staging buffers when the next call refills them
+    auto drain = [&](fse_status st) {
+        cudaStreamSynchronize(h->h2d_stream);
+        cudaStreamSynchronize(stream);
+        cudaStreamSynchronize(h->d2h_stream);
+        return st;
+    };
+#define PIPE_CUDA(call)                                                 \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return drain(cuda_fail(h, e_, #call));   \
+    } while (0)
+    PIPE_CUDA(cudaEventRecord(h->ev_start, stream));
+    PIPE_CUDA(cudaStreamWaitEvent(h->h2d_stream, h->ev_start, 0));
+    PIPE_CUDA(cudaStreamWaitEvent(h->d2h_stream, h->ev_start, 0));
     DevParams P{};
     P.images = h->d_img;
     P.dtype = dtype;
@@ -904,6 +939,8 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
     P.tr_stride = 1;
     P.tw = h->d_tw;
     P.err = h->d_err;
+    P.wait_ns = h->wait_ns;
+    P.clamp_u8 = (h->cfg.flags & FSE_FLAG_CLAMP_U8) ? 1 : 0;
     set_classes(h, P, false);
     const size_t img_frame = (size_t)height * pitch, mask_frame = (size_t)height * width;
     int copied = 0;
@@ -913,21 +950,17 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         // pageable memory the host waits here while chunk c-1 computes)
         if (need[c] > copied) {
             const size_t n = (size_t)(need[c] - copied);
-            FSE_CUDA(h, cudaMemcpyAsync(static_cast<char *>(h->d_img) + copied * img_frame,
+            PIPE_CUDA(cudaMemcpyAsync(static_cast<char *>(h->d_img) + copied * img_frame,
                                         static_cast<const char *>(images) + copied * img_frame, n * img_frame,
                                         cudaMemcpyHostToDevice, h->h2d_stream));
-            FSE_CUDA(h, cudaMemcpyAsync(h->d_mask + copied * mask_frame, loss_mask + copied * mask_frame,
+            PIPE_CUDA(cudaMemcpyAsync(h->d_mask + copied * mask_frame, loss_mask + copied * mask_frame,
                                         n * mask_frame, cudaMemcpyHostToDevice, h->h2d_stream));
             copied = need[c];
         }
         const int n = cs[c + 1] - cs[c];
         Plan pc;
         st = validate_and_plan(h, h->d_img, dtype, n_images, height, width, pitch, h->d_mask, blocks + cs[c], n, pc);
-        if (st != FSE_OK) {
-            cudaStreamSynchronize(h->h2d_stream);
-            cudaStreamSynchronize(stream);
-            return st;
-        }
+        if (st != FSE_OK) return drain(st);
         for (BlockRec &r : pc.sorted) {
             r.orig += cs[c];
             r.patch_off += po[c];
@@ -935,9 +968,9 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         // the sorted list travels on the upload stream too: a copy on the
         // compute stream would queue behind the next chunk's upload
         std::memcpy(h->h_cblocks + cs[c], pc.sorted.data(), (size_t)n * sizeof(BlockRec));
-        FSE_CUDA(h, cudaMemcpyAsync(h->d_cblocks + cs[c], h->h_cblocks + cs[c], (size_t)n * sizeof(BlockRec),
+        PIPE_CUDA(cudaMemcpyAsync(h->d_cblocks + cs[c], h->h_cblocks + cs[c], (size_t)n * sizeof(BlockRec),
                                     cudaMemcpyHostToDevice, h->h2d_stream));
-        FSE_CUDA(h, cudaEventRecord(h->ev_in[c], h->h2d_stream));
+        PIPE_CUDA(cudaEventRecord(h->ev_in[c], h->h2d_stream));
         P.blocks = h->d_cblocks + cs[c];
         P.n_seg = pc.n_seg;
         for (int sg = 0; sg < pc.n_seg; ++sg) {
@@ -949,32 +982,53 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         P.total_items = pc.total_items;
         P.counter = h->d_ccounter + c;
         setup_tma(h, P, pc.ks, dtype, h->d_img, h->d_mask, n_images, height, width, pitch);
-        FSE_CUDA(h, cudaStreamWaitEvent(stream, h->ev_in[c], 0));
+        PIPE_CUDA(cudaStreamWaitEvent(stream, h->ev_in[c], 0));
         int nt = 256, cps = ctas_per_sm(h, pc.ks, 256);
         {   // the autotuner times graph replays of h->params: lend it this chunk's
             const DevParams saved = h->params;
             h->params = P;
             st = autotune(h, pc, stream, &nt, &cps);
             h->params = saved;
-            if (st != FSE_OK) return st;
+            if (st != FSE_OK) return drain(st);
         }
         const int grid = std::max(1, std::min(pc.total_items, cps * h->sm_count));
-        FSE_CUDA(h, cudaMemsetAsync(P.counter, 0, sizeof(int), stream));
-        FSE_CUDA(h, launch_fse(h, pc.ks, nt, grid, P, stream));
-        FSE_CUDA(h, cudaEventRecord(h->ev_k[c], stream));
+        PIPE_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(int), stream));
+        PIPE_CUDA(launch_fse(h, pc.ks, nt, grid, P, stream));
+        PIPE_CUDA(cudaEventRecord(h->ev_k[c], stream));
     }
     // read-backs after every launch is queued (a copy to pageable memory
     // returns only when it is done)
     for (int c = 0; c < K; ++c) {
-        FSE_CUDA(h, cudaStreamWaitEvent(h->d2h_stream, h->ev_k[c], 0));
-        FSE_CUDA(h, cudaMemcpyAsync(patches + po[c], h->d_patch + po[c], (size_t)(po[c + 1] - po[c]) * sizeof(float),
+        PIPE_CUDA(cudaStreamWaitEvent(h->d2h_stream, h->ev_k[c], 0));
+        PIPE_CUDA(cudaMemcpyAsync(patches + po[c], h->d_patch + po[c], (size_t)(po[c + 1] - po[c]) * sizeof(float),
                                     cudaMemcpyDeviceToHost, h->d2h_stream));
     }
-    FSE_CUDA(h, cudaEventRecord(h->ev_out, h->d2h_stream));
-    FSE_CUDA(h, cudaStreamWaitEvent(stream, h->ev_out, 0));
+    PIPE_CUDA(cudaEventRecord(h->ev_out, h->d2h_stream));
+    PIPE_CUDA(cudaStreamWaitEvent(stream, h->ev_out, 0));
+#undef PIPE_CUDA
     h->last_n_blocks = n_blocks;
     h->last_stream = stream;
     FSE_CUDA(h, cudaStreamSynchronize(stream));
+    return FSE_OK;
+}
+
+// A block list in device memory is copied to the handle's host staging on
+// the caller's stream (after the work that may have produced it) and *blocks
+// is pointed there; a host (pageable, pinned or managed) list is used as is.
+fse_status host_block_list(fse_handle *h, const fse_block **blocks, int n_blocks, cudaStream_t stream) {
+    if (n_blocks <= 0 || !*blocks) return FSE_OK;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, *blocks) != cudaSuccess) {
+        cudaGetLastError();   // an unregistered host pointer on older drivers: host memory
+        return FSE_OK;
+    }
+    if (a.type != cudaMemoryTypeDevice) return FSE_OK;
+    if (a.device != h->device) return fail(h, FSE_ERR_INVALID_ARG, "blocks live on device %d, not %d", a.device, h->device);
+    h->hb_stage.resize((size_t)n_blocks);
+    FSE_CUDA(h, cudaMemcpyAsync(h->hb_stage.data(), *blocks, (size_t)n_blocks * sizeof(fse_block),
+                                cudaMemcpyDeviceToHost, stream));
+    FSE_CUDA(h, cudaStreamSynchronize(stream));
+    *blocks = h->hb_stage.data();
     return FSE_OK;
 }
 
@@ -1037,18 +1091,18 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
         CREATE_CUDA(cudaFuncSetAttribute(fse_tc::cnn_tc_kernel<DevParams, BlockRec>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, fse_tc::kSmemBytes));
     }
-    CREATE_CUDA(cudaMalloc(&h->d_err, sizeof(int)));
+    CREATE_CUDA(fse::dev_malloc(&h->d_err, sizeof(int)));
     CREATE_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
     CREATE_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CREATE_CUDA(cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming));
-    CREATE_CUDA(cudaMalloc(&h->d_counter, sizeof(int)));
-    CREATE_CUDA(cudaMalloc(&h->d_tw, 64 * sizeof(float2)));
+    CREATE_CUDA(fse::dev_malloc(&h->d_counter, sizeof(int)));
+    CREATE_CUDA(fse::dev_malloc(&h->d_tw, 64 * sizeof(float2)));
     fse::twiddle_kernel<<<1, 64, 0, h->cap_stream>>>(h->d_tw);
     CREATE_CUDA(cudaGetLastError());
     for (int c = 0; c < cfg->n_classes; ++c) {
         const int M = cfg->cls[c].block + 2 * cfg->cls[c].border;
         const int T = cfg->cls[c].frames > 1 ? cfg->cls[c].frames : 1;
-        CREATE_CUDA(cudaMalloc(&h->d_wtab[c], (size_t)T * M * M * sizeof(float)));
+        CREATE_CUDA(fse::dev_malloc(&h->d_wtab[c], (size_t)T * M * M * sizeof(float)));
         fse::weight_table_kernel<<<(T * M * M + 255) / 256, 256, 0, h->cap_stream>>>(h->d_wtab[c], M, T,
                                                                                     (double)cfg->cls[c].rho);
         CREATE_CUDA(cudaGetLastError());
@@ -1064,8 +1118,11 @@ fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, i
                                  float *out, float *patches, void *cuda_stream) {
     if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
     DeviceGuard guard(h->device);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    fse_status st = host_block_list(h, &blocks, n_blocks, stream);
+    if (st != FSE_OK) return st;
     return run_batch(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks, n_blocks, out,
-                     patches, static_cast<cudaStream_t>(cuda_stream));
+                     patches, stream);
 }
 
 fse_status fse_extrapolate_batch_init(fse_handle *h, const void *images, int dtype, int n_images, int height,
@@ -1084,8 +1141,11 @@ fse_status fse_extrapolate_batch_init(fse_handle *h, const void *images, int dty
     if ((long long)est_stride < maxMM)
         return fail(h, FSE_ERR_INVALID_ARG, "est_stride %zu < largest area %lld", est_stride, maxMM);
     DeviceGuard guard(h->device);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    fse_status st = host_block_list(h, &blocks, n_blocks, stream);
+    if (st != FSE_OK) return st;
     return run_batch(h, images, dtype, n_images, height, width, pitch_bytes, loss_mask, blocks, n_blocks, out,
-                     patches, static_cast<cudaStream_t>(cuda_stream), init_estimate, (long long)est_stride);
+                     patches, stream, init_estimate, (long long)est_stride);
 }
 
 fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n) {
@@ -1097,18 +1157,16 @@ fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(params[i])) return fail(h, FSE_ERR_INVALID_ARG, "parameter %zu is not finite", i);
     DeviceGuard guard(h->device);
-    if (!h->d_cnn_params) {
-        FSE_CUDA(h, cudaMalloc(&h->d_cnn_params, fse_net::kParams * sizeof(float)));
-        FSE_CUDA(h, cudaMalloc(&h->d_cnn_wb, fse_net::kWbTotal * sizeof(__nv_bfloat16)));
-        FSE_CUDA(h, cudaMalloc(&h->d_cnn_wt, fse_net::kWtTotal * sizeof(float)));
-    }
+    if (!h->d_cnn_params) FSE_CUDA(h, fse::dev_malloc(&h->d_cnn_params, fse_net::kParams * sizeof(float)));
+    if (!h->d_cnn_wb) FSE_CUDA(h, fse::dev_malloc(&h->d_cnn_wb, fse_net::kWbTotal * sizeof(__nv_bfloat16)));
+    if (!h->d_cnn_wt) FSE_CUDA(h, fse::dev_malloc(&h->d_cnn_wt, fse_net::kWtTotal * sizeof(float)));
     FSE_CUDA(h, cudaDeviceSynchronize());
     FSE_CUDA(h, cudaMemcpy(h->d_cnn_params, params, n * sizeof(float), cudaMemcpyHostToDevice));
     const int m = std::max(fse_net::kWbTotal, fse_net::kWtTotal);
     fse_net::pack_weights_kernel<<<(m + 255) / 256, 256>>>(h->d_cnn_params, h->d_cnn_wb, h->d_cnn_wt);
     FSE_CUDA(h, cudaGetLastError());
     if (h->tc_net) {
-        if (!h->d_tc_w) FSE_CUDA(h, cudaMalloc(&h->d_tc_w, fse_tc::kWBytes));
+        if (!h->d_tc_w) FSE_CUDA(h, fse::dev_malloc(&h->d_tc_w, fse_tc::kWBytes));
         fse_tc::pack_tc_weights_kernel<<<(fse_tc::kWBytes / 2 + 255) / 256, 256>>>(
             h->d_cnn_params, reinterpret_cast<__nv_bfloat16 *>(h->d_tc_w));
         FSE_CUDA(h, cudaGetLastError());
@@ -1178,6 +1236,23 @@ fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef
     return FSE_OK;
 }
 
+fse_status fse_get_trace_gap(fse_handle *h, float *gap2, size_t cap) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (!(h->cfg.flags & FSE_FLAG_TRACE)) return fail(h, FSE_ERR_INVALID_ARG, "handle was created without FSE_FLAG_TRACE");
+    DeviceGuard guard(h->device);
+    const size_t n = (size_t)h->last_n_blocks * h->tr_stride;
+    if (n == 0) return FSE_OK;
+    if (!gap2) return fail(h, FSE_ERR_INVALID_ARG, "gap2 is NULL");
+    if (cap < n) return fail(h, FSE_ERR_INVALID_ARG, "cap %zu < n_blocks * stride = %zu", cap, n);
+    FSE_CUDA(h, cudaStreamSynchronize(h->last_stream));
+    std::vector<float> e1(n), e2(n);
+    FSE_CUDA(h, cudaMemcpy(e1.data(), h->d_tr_energy, n * sizeof(float), cudaMemcpyDeviceToHost));
+    FSE_CUDA(h, cudaMemcpy(e2.data(), h->d_tr_second, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i)
+        gap2[i] = e1[i] > 0.f ? (float)(((double)e1[i] - (double)e2[i]) / (double)e1[i]) : 0.f;
+    return FSE_OK;
+}
+
 fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, void *cuda_stream) {
     if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
     if (!(h->cfg.flags & FSE_FLAG_TRACE)) return fail(h, FSE_ERR_INVALID_ARG, "handle was created without FSE_FLAG_TRACE");
@@ -1207,8 +1282,24 @@ fse_status fse_sync(fse_handle *h) {
     FSE_CUDA(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e != 0) {
         FSE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
-        return fail(h, FSE_ERR_TIMEOUT, "a bounded wait of the learned-initialisation kernel expired");
+        if (e & fse::kErrTimeout)
+            return fail(h, FSE_ERR_TIMEOUT, "a bounded device wait ran out (limit %llu ns)", h->wait_ns);
+        return fail(h, FSE_ERR_INVALID_ARG, "a lost block's loss area is not marked lost in the loss mask");
     }
+    return FSE_OK;
+}
+
+fse_status fse_set_wait_limit(fse_handle *h, unsigned long long ns) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (ns > 60000000000ull) return fail(h, FSE_ERR_INVALID_ARG, "wait limit %llu ns above 60 s", ns);
+    if (ns != h->wait_ns && h->gexec) {   // the captured launch holds the old limit
+        DeviceGuard guard(h->device);
+        if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->graph_valid = false;
+    }
+    h->wait_ns = ns;
     return FSE_OK;
 }
 
@@ -1220,34 +1311,35 @@ void fse_destroy(fse_handle *h) {
         DeviceGuard guard(h->device);
         if (h->last_stream || h->cap_stream) cudaDeviceSynchronize();
         if (h->gexec) cudaGraphExecDestroy(h->gexec);
-        for (auto &p : h->d_wtab) cudaFree(p);
-        cudaFree(h->d_tw);
-        cudaFree(h->d_counter);
-        cudaFree(h->d_blocks);
-        if (h->h_blocks) cudaFreeHost(h->h_blocks);
-        cudaFree(h->d_tr_sel);
-        cudaFree(h->d_tr_energy);
-        cudaFree(h->d_tr_coef);
-        cudaFree(h->d_img);
-        cudaFree(h->d_mask);
-        cudaFree(h->d_patch);
-        cudaFree(h->d_cnn_params);
-        cudaFree(h->d_cnn_wb);
-        cudaFree(h->d_cnn_wt);
-        cudaFree(h->d_cnn_x);
-        cudaFree(h->d_tc_w);
-        cudaFree(h->d_err);
-        cudaFree(h->d_nb_start);
-        cudaFree(h->d_nb_list);
-        cudaFree(h->d_done);
-        cudaFree(h->d_cnn_a0);
-        cudaFree(h->d_cnn_a1);
-        cudaFree(h->d_cnn_out);
-        cudaFree(h->d_est);
+        for (auto &p : h->d_wtab) fse::dev_free(p);
+        fse::dev_free(h->d_tw);
+        fse::dev_free(h->d_counter);
+        fse::dev_free(h->d_blocks);
+        if (h->h_blocks) fse::host_free(h->h_blocks);
+        fse::dev_free(h->d_tr_sel);
+        fse::dev_free(h->d_tr_energy);
+        fse::dev_free(h->d_tr_coef);
+        fse::dev_free(h->d_tr_second);
+        fse::dev_free(h->d_img);
+        fse::dev_free(h->d_mask);
+        fse::dev_free(h->d_patch);
+        fse::dev_free(h->d_cnn_params);
+        fse::dev_free(h->d_cnn_wb);
+        fse::dev_free(h->d_cnn_wt);
+        fse::dev_free(h->d_cnn_x);
+        fse::dev_free(h->d_tc_w);
+        fse::dev_free(h->d_err);
+        fse::dev_free(h->d_nb_start);
+        fse::dev_free(h->d_nb_list);
+        fse::dev_free(h->d_done);
+        fse::dev_free(h->d_cnn_a0);
+        fse::dev_free(h->d_cnn_a1);
+        fse::dev_free(h->d_cnn_out);
+        fse::dev_free(h->d_est);
         if (h->upload_done) cudaEventDestroy(h->upload_done);
-        cudaFree(h->d_cblocks);
-        if (h->h_cblocks) cudaFreeHost(h->h_cblocks);
-        cudaFree(h->d_ccounter);
+        fse::dev_free(h->d_cblocks);
+        if (h->h_cblocks) fse::host_free(h->h_cblocks);
+        fse::dev_free(h->d_ccounter);
         for (int c = 0; c < kHostChunks; ++c) {
             if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
             if (h->ev_k[c]) cudaEventDestroy(h->ev_k[c]);

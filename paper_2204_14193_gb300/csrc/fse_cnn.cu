@@ -11,6 +11,7 @@
 #include <string>
 
 #include "fse.h"
+#include "fse_alloc.cuh"
 #include "fse_cnn.cuh"
 
 using namespace fse_net;
@@ -146,7 +147,7 @@ fse_status fse_cnn_create(fse_cnn **out, int device, int height, int width, int 
     c->nparts_max = (int)std::min<long long>(1024, std::max<long long>(1, max_batch));
     cudaError_t e = cudaSuccess;
     auto M = [&](void **p, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = fse::dev_malloc(p, bytes);
     };
     M((void **)&c->params, kParams * sizeof(float));
     M((void **)&c->m, kParams * sizeof(float));
@@ -199,6 +200,37 @@ fse_status fse_cnn_get_params(fse_cnn *c, float *params, size_t n) {
     DevGuard guard(c->device);
     CNN_CUDA(c, cudaDeviceSynchronize());
     CNN_CUDA(c, cudaMemcpy(params, c->params, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return FSE_OK;
+}
+
+fse_status fse_cnn_get_state(fse_cnn *c, float *params, float *m, float *v, long long *step) {
+    if (!c) return cfail(nullptr, FSE_ERR_INVALID_ARG, "cnn handle is NULL");
+    if (!params || !m || !v || !step) return cfail(c, FSE_ERR_INVALID_ARG, "a state pointer is NULL");
+    DevGuard guard(c->device);
+    CNN_CUDA(c, cudaDeviceSynchronize());
+    CNN_CUDA(c, cudaMemcpy(params, c->params, kParams * sizeof(float), cudaMemcpyDeviceToHost));
+    CNN_CUDA(c, cudaMemcpy(m, c->m, kParams * sizeof(float), cudaMemcpyDeviceToHost));
+    CNN_CUDA(c, cudaMemcpy(v, c->v, kParams * sizeof(float), cudaMemcpyDeviceToHost));
+    *step = c->step;
+    return FSE_OK;
+}
+
+fse_status fse_cnn_set_state(fse_cnn *c, const float *params, const float *m, const float *v, long long step) {
+    if (!c) return cfail(nullptr, FSE_ERR_INVALID_ARG, "cnn handle is NULL");
+    if (!params || !m || !v) return cfail(c, FSE_ERR_INVALID_ARG, "a state pointer is NULL");
+    if (step < 0 || step > (1LL << 24)) return cfail(c, FSE_ERR_INVALID_ARG, "step %lld not in [0, 2^24]", step);
+    for (int i = 0; i < kParams; ++i)
+        if (!std::isfinite(params[i]) || !std::isfinite(m[i]) || !(v[i] >= 0.f) || !std::isfinite(v[i]))
+            return cfail(c, FSE_ERR_INVALID_ARG, "state entry %d is not finite (or v < 0)", i);
+    DevGuard guard(c->device);
+    CNN_CUDA(c, cudaDeviceSynchronize());
+    CNN_CUDA(c, cudaMemcpy(c->params, params, kParams * sizeof(float), cudaMemcpyHostToDevice));
+    CNN_CUDA(c, cudaMemcpy(c->m, m, kParams * sizeof(float), cudaMemcpyHostToDevice));
+    CNN_CUDA(c, cudaMemcpy(c->v, v, kParams * sizeof(float), cudaMemcpyHostToDevice));
+    c->step = (int)step;
+    fse_status st = pack(c, nullptr);
+    if (st != FSE_OK) return st;
+    CNN_CUDA(c, cudaDeviceSynchronize());
     return FSE_OK;
 }
 
@@ -266,21 +298,21 @@ void fse_cnn_destroy(fse_cnn *c) {
     {
         DevGuard guard(c->device);
         cudaDeviceSynchronize();
-        cudaFree(c->params);
-        cudaFree(c->m);
-        cudaFree(c->v);
-        cudaFree(c->grad);
-        cudaFree(c->wb);
-        cudaFree(c->wt);
-        cudaFree(c->xin);
-        for (auto a : c->act) cudaFree(a);
-        cudaFree(c->y);
-        cudaFree(c->gy);
-        cudaFree(c->g0);
-        cudaFree(c->g1);
-        cudaFree(c->part);
-        cudaFree(c->lpart);
-        cudaFree(c->loss);
+        fse::dev_free(c->params);
+        fse::dev_free(c->m);
+        fse::dev_free(c->v);
+        fse::dev_free(c->grad);
+        fse::dev_free(c->wb);
+        fse::dev_free(c->wt);
+        fse::dev_free(c->xin);
+        for (auto a : c->act) fse::dev_free(a);
+        fse::dev_free(c->y);
+        fse::dev_free(c->gy);
+        fse::dev_free(c->g0);
+        fse::dev_free(c->g1);
+        fse::dev_free(c->part);
+        fse::dev_free(c->lpart);
+        fse::dev_free(c->loss);
     }
     delete c;
 }

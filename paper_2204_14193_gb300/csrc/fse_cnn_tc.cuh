@@ -35,8 +35,9 @@
 //     im2col in the same plane layout;
 //   - layer 3 (1 output channel) runs with N = 16 (zero weights beyond
 //     channel 0) and its epilogue writes 255 x (acc + bias) on B.
-// Waits on the mbarrier are bounded (1 s of globaltimer); on expiry the
-// kernel records FSE_ERR_TIMEOUT in *err, stops, and frees its TMEM.
+// Waits on the mbarrier are bounded (the handle's wait limit, 1 s by default,
+// of globaltimer); on expiry the kernel records the timeout in *err, waits
+// (at most 1 s) for the MMAs it has committed, frees its TMEM and stops.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -143,6 +144,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// the same test without blocking (a single poll)
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 
 // one FP32 accumulator column of this warp's 32 TMEM lanes (the wait names
 // the register, so no use of it can be scheduled before the load completes)
@@ -201,14 +214,18 @@ struct Shared {
     volatile int *flag;
 };
 
-// thread 0 waits for the committed MMAs (bounded), every thread learns the
-// outcome after the barrier
-__device__ __forceinline__ bool wait_mma(const Shared &S, uint32_t parity) {
+// thread 0 waits for the committed MMAs (bounded by limit_ns), every thread
+// learns the outcome after the barrier
+__device__ __forceinline__ bool wait_mma(const Shared &S, uint32_t parity, unsigned long long limit_ns) {
     if (threadIdx.x == 0) {
-        const uint64_t t0 = globaltimer();
-        bool done = false;
-        while (!(done = mbar_try_wait(S.bar, parity)))
-            if (globaltimer() - t0 > 1000000000ull) break;
+        // the first poll does not block: a limit of 0 expires as soon as the
+        // MMAs are found unfinished
+        bool done = mbar_test_wait(S.bar, parity);
+        if (!done && limit_ns > 0) {
+            const uint64_t t0 = globaltimer();
+            while (!(done = mbar_try_wait(S.bar, parity)))
+                if (globaltimer() - t0 > limit_ns) break;
+        }
         *S.flag = done ? 0 : 1;
     }
     __syncthreads();
@@ -405,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             mma_commit(S.bar);
         }
-        if (!(ok = wait_mma(S, parity))) break;
+        if (!(ok = wait_mma(S, parity, P.wait_ns))) break;
         parity ^= 1u;
         epilogue_hidden<0>(S, tmem);
         fence_proxy_async();
@@ -416,14 +433,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         // while layer 1 runs: the next area's input (xs is free since the im2col)
         if (warp >= kIssuers && qb + (int)gridDim.x < n_blocks)
             stage_input(P, P.blocks[qb + gridDim.x], S.xs, 32 * kIssuers);
-        if (!(ok = wait_mma(S, parity))) break;
+        if (!(ok = wait_mma(S, parity, P.wait_ns))) break;
         parity ^= 1u;
         epilogue_hidden<1>(S, tmem);
         fence_proxy_async();
         fence_before_sync();
         __syncthreads();
         if (warp < kIssuers) { fence_after_sync(); issue_layer<2>(S, tmem, warp); }
-        if (!(ok = wait_mma(S, parity))) break;
+        if (!(ok = wait_mma(S, parity, P.wait_ns))) break;
         parity ^= 1u;
         epilogue_hidden<2>(S, tmem);
         fence_proxy_async();
@@ -431,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         // ---- layer 3: channel 0 on B ----
         if (warp < kIssuers) { fence_after_sync(); issue_layer<3>(S, tmem, warp); }
-        if (!(ok = wait_mma(S, parity))) break;
+        if (!(ok = wait_mma(S, parity, P.wait_ns))) break;
         parity ^= 1u;
         if (warp < 4) {
             const float b3 = S.bias[96];
@@ -445,7 +462,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before_sync();
         __syncthreads();   // TMEM and the planes are reused by the next area
     }
-    if (!ok && tid == 0) atomicExch(err, 5);
+    if (!ok && tid == 0) {
+        // expired: report it (bit 1 of the status word, the timeout bit the
+        // concealment kernel uses too), then let the MMAs of the last commit
+        // finish, bounded by 1 s, before the tensor memory is freed
+        atomicOr(err, 1);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(S.bar, parity) && globaltimer() - t0 < 1000000000ull) {
+        }
+    }
     fence_before_sync();
     __syncthreads();
     if (warp == 0) {

@@ -73,6 +73,7 @@ struct DevParams {
     int *tr_sel;                      // trace (nullptr = off)
     float *tr_energy;
     float2 *tr_coef;
+    float *tr_second;                 // trace: largest |R_w|^2 besides the pick (nullptr = off)
     int tr_stride;
     const float2 *tw;                 // 64 entries (cos, sin)(2 pi t / 64)
     const float *est;                 // warm start: per-block estimate (sample units) or nullptr
@@ -83,7 +84,9 @@ struct DevParams {
     float beta;                       // weight factor of reused samples
     const int *nb_start, *nb_list;    // CSR: earlier blocks whose B meets the block's area
     int *done;                        // per block: concealed output visible (zeroed per launch)
-    int *err;                         // device status word (a bounded wait expired: 5)
+    int *err;                         // device status word: kErr* bits (nullptr: not reported)
+    unsigned long long wait_ns;       // limit of every bounded device wait
+    int clamp_u8;                     // outputs clamped to [0, 255] and rounded half to even
     // F = 64 windows of 8-bit images fetched as tiles by the tensor-memory
     // accelerator: 2-D maps over [n_images * H rows, W columns] of the images
     // and the mask, box tma_bw columns x tma_bh rows (tma = 0: plain loads)
@@ -91,6 +94,17 @@ struct DevParams {
     int tma_bw, tma_bh;
     CUtensorMap tm_img, tm_mask;
 };
+
+// bits of the device status word (read and cleared by fse_sync)
+constexpr int kErrTimeout = 1;    // a bounded wait ran out
+constexpr int kErrUnmarked = 2;   // a block's loss area B is not marked lost in the mask
+// after an expired wait the kernel still waits this long, at most, for its
+// own asynchronous copies in flight
+constexpr unsigned long long kDrainNs = 1000000000ull;
+
+__device__ __forceinline__ void report(const DevParams &P, int bit) {
+    if (P.err != nullptr) atomicOr(P.err, bit);
+}
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -225,6 +239,7 @@ constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2;
 struct RedShared {
     uint4 win[2][kMaxWarps];   // per-warp argmax candidates, double-buffered by iteration parity
     float sum[kMaxWarps];
+    uint32_t sec[2][kMaxWarps];   // per-warp second-largest energies (traced launches)
     unsigned long long mbar;   // completion barrier of the window tiles (TMA gather)
 };
 
@@ -250,13 +265,24 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
-// Wait for phase `parity` of bar, bounded by 1 s of %globaltimer; false if
-// the wait ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+// Wait for phase `parity` of bar, bounded by limit_ns of %globaltimer; false
+// if the wait ran out.  The first poll does not block (test_wait), so a
+// limit of 0 expires as soon as the phase is found incomplete; later polls
+// use try_wait, which may suspend the thread for a while.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long limit_ns) {
     const uint32_t a = smem_u32(bar);
-    uint64_t t0 = 0;
-    for (int spin = 0;; ++spin) {
-        uint32_t ok;
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (limit_ns == 0) return false;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -265,10 +291,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
-        uint64_t t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (spin == 0) t0 = t;
-        else if (t - t0 > 1000000000ull) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -394,7 +417,21 @@ struct Pick {
     uint32_t idx;
     float rr, ri;
     uint32_t ebits;
+    uint32_t sbits;   // largest energy of the other bins (traced launches only)
 };
+
+// The largest energy of this thread's bins other than slot `skip` (the
+// energies are recomputed with the loop's own instruction sequence).
+template <int PAIRS>
+__device__ __forceinline__ uint32_t thread_second(const uint64_t *Rre, const uint64_t *Rim, int skip) {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < PAIRS; ++i) {
+        const uint64_t e = energy2(Rre[i], Rim[i]);
+        m = max3f(m, 2 * i == skip ? 0.f : lo_of(e), 2 * i + 1 == skip ? 0.f : hi_of(e));
+    }
+    return __float_as_uint(m);
+}
 
 // Find, in one thread, the first (smallest linear index) of its bins whose
 // energy bits equal M, searching only quartet J (pairs 4J .. 4J+3).
@@ -449,9 +486,11 @@ __device__ __forceinline__ void quartet_max(int j, float qj, float &tmax, int &j
 // so the reduction is built from as few DEPENDENT such steps as possible:
 // one redux.sync for the max, the owner's register search, one redux.sync for
 // the smallest index, and (multi-warp groups) one shared-memory exchange.
-template <int F, int PAIRS, int NT, int FT = 1>
+// GAP (compiled in) and gap (at run time): also the largest energy of the
+// other bins, for the trace's top-two gap.
+template <int F, int PAIRS, int NT, int FT = 1, bool GAP = false>
 __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t *Rim, float tmax, int jb,
-                                             const Grp &gr, RedShared *rs, int parity) {
+                                             const Grp &gr, RedShared *rs, int parity, bool gap = false) {
     using G = Geo<F, PAIRS, FT>;
     const uint32_t mt = __float_as_uint(tmax);
     const int c0 = gr.lt % G::LPR, r0 = gr.lt / G::LPR;
@@ -469,14 +508,22 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         const uint32_t mw = __reduce_max_sync(0xffffffffu, mt);
         uint32_t cand = 0xffffffffu;
         float rr = 0.f, ri = 0.f;
+        int hit = -1;
         if (mt == mw) {
-            const int hit = thread_search<G::NQ>(Rre, Rim, jb, mw, rr, ri);
+            hit = thread_search<G::NQ>(Rre, Rim, jb, mw, rr, ri);
             if (hit >= 0) cand = lin(hit);
         }
         const uint32_t iw = __reduce_min_sync(0xffffffffu, cand);
         uint4 *win = rs->win[parity];
-        if ((cand == iw && cand != 0xffffffffu) || (iw == 0xffffffffu && lane == 0))
-            win[warp] = make_uint4(mw, iw, __float_as_uint(rr), __float_as_uint(ri));
+        const bool writer = (cand == iw && cand != 0xffffffffu) || (iw == 0xffffffffu && lane == 0);
+        if (writer) win[warp] = make_uint4(mw, iw, __float_as_uint(rr), __float_as_uint(ri));
+        if constexpr (GAP) {
+            if (gap) {   // the warp's second: the candidate's owner without the candidate, the others' maxima
+                const uint32_t sl = (cand == iw && cand != 0xffffffffu) ? thread_second<PAIRS>(Rre, Rim, hit) : mt;
+                const uint32_t sw = __reduce_max_sync(0xffffffffu, sl);
+                if (writer) rs->sec[parity][warp] = sw;
+            }
+        }
         gsync<F, PAIRS, NT, FT>(gr);
         // the warps' candidates combined as a tree (log2 WPG dependent steps;
         // the order (larger energy, then smaller index) is total, so any
@@ -492,6 +539,16 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 #pragma unroll
             for (int i = 0; i + s < G::WPG; i += 2 * s) e[i] = better(e[i], e[i + s]);
         p.ebits = e[0].x; p.idx = e[0].y; p.rr = __uint_as_float(e[0].z); p.ri = __uint_as_float(e[0].w);
+        p.sbits = 0u;
+        if constexpr (GAP) {
+            if (gap) {   // the winning warp contributes its second, the others their maxima
+#pragma unroll
+                for (int i = 0; i < G::WPG; ++i) {
+                    const uint4 c = win[w0 + i];
+                    p.sbits = max(p.sbits, c.y == p.idx ? rs->sec[parity][w0 + i] : c.x);
+                }
+            }
+        }
     } else {
         constexpr int W = G::LANES;               // lanes of one group (8, 16 or 32)
         constexpr int NG = 32 / W;                // groups per warp
@@ -505,8 +562,9 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         }
         uint32_t cand = 0xffffffffu;
         float rr = 0.f, ri = 0.f;
+        int hit = -1;
         if (mt == M) {
-            const int hit = thread_search<G::NQ>(Rre, Rim, jb, M, rr, ri);
+            hit = thread_search<G::NQ>(Rre, Rim, jb, M, rr, ri);
             if (hit >= 0) cand = lin(hit);
         }
         uint32_t iw = 0xffffffffu;
@@ -522,6 +580,17 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
         p.rr = __shfl_sync(gr.amask, rr, src);
         p.ri = __shfl_sync(gr.amask, ri, src);
         p.ebits = M;
+        p.sbits = 0u;
+        if constexpr (GAP) {
+            if (gap) {   // the owner of the pick without it, the group's other lanes their maxima
+                const uint32_t sl = (cand == iw && cand != 0xffffffffu) ? thread_second<PAIRS>(Rre, Rim, hit) : mt;
+#pragma unroll
+                for (int k = 0; k < NG; ++k) {
+                    const uint32_t r = __reduce_max_sync(gr.amask, mygrp == k ? sl : 0u);
+                    if (mygrp == k) p.sbits = r;
+                }
+            }
+        }
     }
     if (p.idx == 0xffffffffu) { p.idx = 0; p.rr = 0.f; p.ri = 0.f; }
     return p;
@@ -530,7 +599,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 // ------------------------------------------------------- per-block worker
 // NP: B samples per thread (compile time; the caller picks the smallest
 // variant that covers b*b).  EXT: built with ordered concealment.
-template <int F, int PAIRS, int NT, int NP, bool EXT = false>
+template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh, uint32_t &tph) {
     using G = Geo<F, PAIRS>;
@@ -559,8 +628,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
                 const uint64_t t0 = globaltimer_ns();
                 for (int q = nb0; q < nb1; ++q)
                     while (ld_acquire_gpu(&P.done[P.nb_list[q]]) == 0) {
-                        if (globaltimer_ns() - t0 > 1000000000ull) {
-                            atomicExch(P.err, 5);
+                        if (globaltimer_ns() - t0 > P.wait_ns) {
+                            report(P, kErrTimeout);
                             break;
                         }
                         __nanosleep(128);
@@ -591,7 +660,12 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             tma_load_2d(stage, &P.tm_img, x0, blk.image * P.H + blk.y - d, &rsh->mbar);
             tma_load_2d(stage + moff, &P.tm_mask, x0, blk.image * P.H + blk.y - d, &rsh->mbar);
         }
-        if (!mbar_wait(&rsh->mbar, tph)) atomicExch(P.err, 5);
+        if (!mbar_wait(&rsh->mbar, tph, P.wait_ns)) {
+            // expired: report it, then let the copies in flight land (bounded)
+            // before the region is reused
+            report(P, kErrTimeout);
+            mbar_wait(&rsh->mbar, tph, kDrainNs);
+        }
         tph ^= 1u;
 #pragma unroll
         for (int t = 0; t < NPOS; ++t) {
@@ -615,12 +689,14 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         }
     }
     float smax = 0.f;
+    bool unmarked = false;   // a sample of the block's own B not marked lost
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
         const int pix = lt + t * TB;
         const int m = pix / F, n = pix % F;
         const int am = m - off, an = n - off;
         const int yy = blk.y - d + am, xx = blk.x - d + an;
+        unmarked |= am >= d && am < d + b && an >= d && an < d + b && mk[t] == 0;
         bool inA = am >= 0 && am < M && an >= 0 && an < M &&
                    !(am >= d && am < d + b && an >= d && an < d + b) &&
                    yy >= 0 && yy < P.H && xx >= 0 && xx < P.W && mk[t] == 0;
@@ -649,6 +725,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         if (inA) smax = fmaxf(smax, fabsf(sr));
         Z[m * FP + n] = make_float2(ws, w);
     }
+    if (unmarked) report(P, kErrUnmarked);
     // alpha = the power of two in (max|s| / 2, max|s|] over the support:
     // balances the two real signals packed into one complex FFT (an exact
     // scaling; a maximum, so it is independent of the thread mapping)
@@ -739,7 +816,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     }
     const int iters = C.iters;
     Pick pick;
-    if (iters > 0) pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, jb, gr, rsh, 0);
+    const bool gap = GAP && P.tr_second != nullptr;
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, 0, gap);
 
     const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
     for (int nu = 1; nu <= iters; ++nu) {
@@ -751,6 +829,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             P.tr_sel[o] = (int)pick.idx;
             P.tr_energy[o] = __uint_as_float(pick.ebits);
             P.tr_coef[o] = make_float2(cr, ci);
+            if (GAP && P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
         }
         // model update of this selection, evaluated on B: g += c phi_(u,v)
         // (independent of the residual update and of the next reduction)
@@ -807,7 +886,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         }
         model();
         // ---- S5: next selection ----
-        pick = group_argmax<F, PAIRS, NT>(Rre, Rim, tmax, jb, gr, rsh, nu & 1);
+        pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, nu & 1, gap);
     }
 
     // ---- S10: write Re{g} on B ----
@@ -816,8 +895,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         const int j = lt + t * TB;
         if (j < b * b) {
             const int pm = j / b, pn = j % b;
-            const float val =
-                acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
+            float val = acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
+            if (P.clamp_u8) val = rintf(fminf(fmaxf(val, 0.f), 255.f));
             if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
             if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
         }
@@ -836,7 +915,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
 // -- Algorithm 1 with 3-D basis functions and 3-D circular shifts.  (Kept
 // apart from process() so that the image path's code is not touched by the
 // temporal dimension.)
-template <int F, int PAIRS, int NT, int NP, int FT>
+template <int F, int PAIRS, int NT, int NP, int FT, bool GAP = false>
 __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &C, int first, int count,
                                             unsigned char *smem, const float2 *s_tw, RedShared *rsh) {
     static_assert(FT > 1, "image areas run process()");
@@ -866,8 +945,8 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
             const uint64_t t0 = globaltimer_ns();
             for (int q = nb0; q < nb1; ++q)
                 while (ld_acquire_gpu(&P.done[P.nb_list[q]]) == 0) {
-                    if (globaltimer_ns() - t0 > 1000000000ull) {
-                        atomicExch(P.err, 5);
+                    if (globaltimer_ns() - t0 > P.wait_ns) {
+                        report(P, kErrTimeout);
                         break;
                     }
                     __nanosleep(128);
@@ -897,6 +976,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
                              : reinterpret_cast<const float *>(row)[xx];
     }
     float smax = 0.f;
+    bool unmarked = false;   // a sample of the block's own B not marked lost
 #pragma unroll
     for (int t = 0; t < NPOS; ++t) {
         const int pix = lt + t * TB;
@@ -907,6 +987,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         const int tau = pl - C.toff;                       // frame of the volume (FT = 1: 0)
         const int fr = blk.image + tau - C.tc;
         const bool own = tau == C.tc && am >= d && am < d + b && an >= d && an < d + b;
+        unmarked |= own && mk[t] == 0;
         const bool inV = am >= 0 && am < M && an >= 0 && an < M && !own && yy >= 0 && yy < P.H && xx >= 0 &&
                          xx < P.W && (FT == 1 || (tau >= 0 && tau < C.T && fr >= 0 && fr < P.n_images));
         // ordered: a lost sample of an earlier block is reused at its concealed value
@@ -930,6 +1011,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     // alpha = the power of two in (max|s| / 2, max|s|] over the support:
     // balances the two real signals packed into one complex FFT (an exact
     // scaling; a maximum, so it is independent of the thread mapping)
+    if (unmarked) report(P, kErrUnmarked);
     const float tmaxs = group_max<F, PAIRS, NT, FT>(smax, gr, rsh);
     float alpha = 1.f;
     if (tmaxs > 0.f) {
@@ -1021,7 +1103,8 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     }
     const int iters = C.iters;
     Pick pick;
-    if (iters > 0) pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, jb, gr, rsh, 0);
+    const bool gap = GAP && P.tr_second != nullptr;
+    if (iters > 0) pick = group_argmax<F, PAIRS, NT, FT, GAP>(Rre, Rim, tmax, jb, gr, rsh, 0, gap);
 
     const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
     for (int nu = 1; nu <= iters; ++nu) {
@@ -1036,6 +1119,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
             P.tr_sel[o] = (int)pick.idx;
             P.tr_energy[o] = __uint_as_float(pick.ebits);
             P.tr_coef[o] = make_float2(cr, ci);
+            if (GAP && P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
         }
         // model update of this selection, evaluated on B: g += c phi_(u,v)
         // (independent of the residual update and of the next reduction)
@@ -1102,7 +1186,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         }
         model();
         // ---- S5: next selection ----
-        pick = group_argmax<F, PAIRS, NT, FT>(Rre, Rim, tmax, jb, gr, rsh, nu & 1);
+        pick = group_argmax<F, PAIRS, NT, FT, GAP>(Rre, Rim, tmax, jb, gr, rsh, nu & 1, gap);
     }
 
     // ---- S10: write Re{g} on B ----
@@ -1111,8 +1195,8 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         const int j = lt + t * TB;
         if (j < b * b) {
             const int pm = j / b, pn = j % b;
-            const float val =
-                acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
+            float val = acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
+            if (P.clamp_u8) val = rintf(fminf(fmaxf(val, 0.f), 255.f));
             if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
             if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
         }
@@ -1124,7 +1208,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     }
 }
 
-template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false>
+template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false, bool GAP = false>
 __device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
                                               unsigned char *smem, const float2 *s_tw, RedShared *rsh,
                                               uint32_t &tph) {
@@ -1132,13 +1216,13 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
     if constexpr (FT == 1) {
         constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
         constexpr int NPL = PAIRS / 2;                // covers b <= F/2
-        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT>(P, C, first, count, smem, s_tw, rsh, tph);
-        else process<F, PAIRS, NT, NPL, EXT>(P, C, first, count, smem, s_tw, rsh, tph);
+        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT, GAP>(P, C, first, count, smem, s_tw, rsh, tph);
+        else process<F, PAIRS, NT, NPL, EXT, GAP>(P, C, first, count, smem, s_tw, rsh, tph);
     } else {
         // a volume's block group is FT times larger: b <= F/2 needs
         // F^2/4 / TB = PAIRS / (2 FT) samples per thread (at least 1)
         constexpr int NPV = PAIRS / (2 * FT) > 0 ? PAIRS / (2 * FT) : 1;
-        process_vol<F, PAIRS, NT, NPV, FT>(P, C, first, count, smem, s_tw, rsh);
+        process_vol<F, PAIRS, NT, NPV, FT, GAP>(P, C, first, count, smem, s_tw, rsh);
     }
 }
 
@@ -1147,7 +1231,8 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
 // most three CTAs per SM.  KS selects what the instantiation carries:
 //   kSetImage  image classes of every FFT size (16, 32, 64)
 //   kSetExt    also video volumes and ordered concealment
-//   kSetF64    image classes of FFT size 64 only
+//   kSetF64    image classes of FFT size 64 only, without the trace's
+//              top-two gap (traced batches run kSetImage)
 // A batch runs the smallest set that covers its classes, so the code and
 // register allocation of the common cases are not burdened by the others.
 template <int NT, int KS>
@@ -1175,16 +1260,16 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
         const int count = min(C.bpi, P.seg_block_start[sg] + P.seg_block_count[sg] - first);
         if (EXT && C.FT == 4) {
             if constexpr (EXT) {
-                if (C.F == 32) process_class<32, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh, tph);
-                else process_class<16, PAIRS, NT, 4, true>(P, C, first, count, smem, s_tw, &rsh, tph);
+                if (C.F == 32) process_class<32, PAIRS, NT, 4, true, true>(P, C, first, count, smem, s_tw, &rsh, tph);
+                else process_class<16, PAIRS, NT, 4, true, true>(P, C, first, count, smem, s_tw, &rsh, tph);
             }
         } else if constexpr (KS == kSetF64) {
             process_class<64, PAIRS, NT, 1, false>(P, C, first, count, smem, s_tw, &rsh, tph);
         } else {
             switch (C.F) {
-                case 64: process_class<64, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh, tph); break;
-                case 32: process_class<32, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh, tph); break;
-                default: process_class<16, PAIRS, NT, 1, EXT>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                case 64: process_class<64, PAIRS, NT, 1, EXT, true>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                case 32: process_class<32, PAIRS, NT, 1, EXT, true>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                default: process_class<16, PAIRS, NT, 1, EXT, true>(P, C, first, count, smem, s_tw, &rsh, tph); break;
             }
         }
         __syncthreads();

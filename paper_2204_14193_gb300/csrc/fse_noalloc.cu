@@ -232,6 +232,7 @@ extern "C" fse_status fse_extrapolate_batch_noalloc(const fse_class *classes, in
     P.tr_coef = nullptr;
     P.tr_stride = 1;
     P.tw = d_tw;
+    P.wait_ns = fse::kDrainNs;   // no bounded wait runs here (no TMA gather, no ordering)
 
     // ---- enqueue: tables, block list, queue head, persistent kernel ----
     fse::twiddle_kernel<<<1, 64, 0, stream>>>(d_tw);

@@ -13,6 +13,7 @@
 #include <cstdio>
 
 #include "fse.h"
+#include "fse_alloc.cuh"
 
 void fse_internal_set_global_error(const char *msg);   // fse_api.cu: text of fse_last_error(NULL)
 
@@ -68,7 +69,7 @@ extern "C" fse_status fse_measure_smem_bandwidth(int device, double *gbytes_per_
     float ms = 0.f;
     const int rounds = 4096;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaMalloc(&d_out, sizeof(unsigned) * sms) != cudaSuccess ||
+        fse::dev_malloc(&d_out, sizeof(unsigned) * sms) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         st = FSE_ERR_CUDA;
@@ -93,7 +94,7 @@ extern "C" fse_status fse_measure_smem_bandwidth(int device, double *gbytes_per_
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (s) cudaStreamDestroy(s);
-    if (d_out) cudaFree(d_out);
+    if (d_out) fse::dev_free(d_out);
     if (prev >= 0) cudaSetDevice(prev);
     return st;
 }

@@ -55,6 +55,19 @@ def weights_path() -> str:
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", WEIGHTS_NAME + ".f32")
 
 
+def shipped_networks():
+    """(k, path) of every shipped network: the one of weights_path() trained
+    for k = 50 iterations after it, and <name>_k<k>.f32 for other k."""
+    import glob
+    import re
+    out = [(50, weights_path())] if os.path.exists(weights_path()) else []
+    for p in sorted(glob.glob(os.path.join(os.path.dirname(weights_path()), WEIGHTS_NAME + "_k*.f32"))):
+        m = re.search(r"_k(\d+)\.f32$", p)
+        if m:
+            out.append((int(m.group(1)), p))
+    return sorted(out)
+
+
 def load_weights(path: str | None = None) -> np.ndarray:
     from . import FSE_CNN_PARAMS
     p = np.fromfile(path or weights_path(), dtype="<f4")
@@ -187,19 +200,42 @@ def training_set(frames, mask, blocks, lam_b: float, target: str = "model", shor
     return x, t.contiguous(), lam.contiguous()
 
 
-def train(x, t, lam, steps: int, batch: int, lr: float, seed: int, init=None, log_every: int = 500):
+def train(x, t, lam, steps: int, batch: int, lr: float, seed: int, init=None, log_every: int = 500,
+          checkpoint: str | None = None, checkpoint_every: int = 0, resume: str | None = None, stop_at=None):
     """Adam on random minibatches with a cosine learning-rate decay; returns
-    the parameters and the loss history."""
+    the parameters and the loss history.
+
+    checkpoint / checkpoint_every: every checkpoint_every steps (and at the
+    end) the whole state -- parameters, Adam moments and step count, the
+    minibatch generator's state, the loop position and the loss history -- is
+    written to checkpoint (.npz).  resume: continue from such a file; the run
+    then goes on bit for bit as if it had not stopped.  stop_at: end the loop
+    after that many steps (a run cut short, to be resumed)."""
     import torch
     from . import Cnn, he_init
     net = Cnn(M, M, max_batch=batch)
-    net.set_params(he_init(seed) if init is None else init)
     g = torch.Generator(device=x.device)
     g.manual_seed(seed)
-    hist = []
-    run = 0.0
+    hist, k0 = [], 0
+    if resume is not None:
+        z = np.load(resume)
+        if int(z["steps"]) != steps or int(z["batch"]) != batch or float(z["lr"]) != lr or int(z["seed"]) != seed:
+            raise ValueError(f"{resume}: checkpoint of another run (steps, batch, lr or seed differ)")
+        net.set_state(z["params"], z["m"], z["v"], int(z["adam_step"]))
+        g.set_state(torch.from_numpy(z["rng"]).to(torch.uint8))
+        k0 = int(z["k"])
+        hist = [tuple(h) for h in z["hist"].tolist()]
+    else:
+        net.set_params(he_init(seed) if init is None else init)
+
+    def save(k):
+        p, m, v, st = net.get_state()
+        np.savez(checkpoint, params=p, m=m, v=v, adam_step=st, rng=g.get_state().numpy(), k=k,
+                 hist=np.array(hist, dtype=np.float64).reshape(-1, 3), steps=steps, batch=batch, lr=lr, seed=seed)
+
     t0 = time.time()
-    for k in range(steps):
+    end = steps if stop_at is None else min(steps, stop_at)
+    for k in range(k0, end):
         idx = torch.randint(0, x.shape[0], (batch,), device=x.device, generator=g)
         lr_k = 1e-5 + 0.5 * (lr - 1e-5) * (1.0 + math.cos(math.pi * k / steps))
         want = (k + 1) % log_every == 0 or k == steps - 1
@@ -208,6 +244,10 @@ def train(x, t, lam, steps: int, batch: int, lr: float, seed: int, init=None, lo
         if want:
             hist.append((k + 1, float(loss), time.time() - t0))
             print(f"step {k + 1}: loss {float(loss):.6g} lr {lr_k:.3g} {time.time() - t0:.1f}s", flush=True)
+        if checkpoint and checkpoint_every and (k + 1) % checkpoint_every == 0:
+            save(k + 1)
+    if checkpoint:
+        save(end)
     p = net.get_params()
     net.close()
     return p, hist
@@ -253,6 +293,9 @@ def main(argv=None):
     ap.add_argument("--short-iters", type=int, default=50)
     ap.add_argument("--init", default=None, help="start from these parameters (.f32)")
     ap.add_argument("--eval-only", default=None, help="evaluate these parameters (.f32) and exit")
+    ap.add_argument("--checkpoint-every", type=int, default=0,
+                    help="write <out>/train_state.npz every this many steps (0: only at the end)")
+    ap.add_argument("--resume", default=None, help="continue the training run of this train_state.npz")
     a = ap.parse_args(argv)
     import torch
     if a.eval_only:
@@ -266,17 +309,20 @@ def main(argv=None):
     del fr, mk
     print(f"training set: {x.shape[0]} areas, {time.time() - t0:.1f}s", flush=True)
     params, hist = train(x, t, lam, a.steps, a.batch, a.lr, a.seed,
-                         init=None if a.init is None else load_weights(a.init))
+                         init=None if a.init is None else load_weights(a.init),
+                         checkpoint=os.path.join(a.out, "train_state.npz"), checkpoint_every=a.checkpoint_every,
+                         resume=a.resume)
     train_s = hist[-1][2] if hist else 0.0
     del x, t, lam
     torch.cuda.empty_cache()
     fr, mk, bl = frames_and_losses(TEST_SEED0, a.test_frames, a.height, a.width, a.loss)
-    ev = evaluate(fr, mk, bl, params)
+    ev = evaluate(fr, mk, bl, params, learned_iters=(0, a.short_iters))
     print(json.dumps(ev), flush=True)
-    params.astype("<f4").tofile(os.path.join(a.out, WEIGHTS_NAME + ".f32"))
+    name = WEIGHTS_NAME if (a.target != "correction" or a.short_iters == 50) else f"{WEIGHTS_NAME}_k{a.short_iters}"
+    params.astype("<f4").tofile(os.path.join(a.out, name + ".f32"))
     meta = dict(vars(a), train_seed0=TRAIN_SEED0, test_seed0=TEST_SEED0, block=B, border=D, fft=FFT, rho=RHO,
                 gamma=GAMMA, train_seconds=train_s, loss_history=hist, eval=ev)
-    with open(os.path.join(a.out, WEIGHTS_NAME + ".json"), "w") as f:
+    with open(os.path.join(a.out, name + ".json"), "w") as f:
         json.dump(meta, f, indent=1)
 
 
