@@ -203,6 +203,14 @@ def job_throughput(ms_local: float, units_local: int, device):
     return ms_max, units, units / (ms_max / 1e3)
 
 
+def smem_bytes_per_block(F: int, I: int) -> float:
+    """Algorithmic shared-memory bytes of one F x F block at I iterations:
+    one 8-byte W operand per bin and iteration, and twelve 8-byte sweeps of
+    the grid for the weighting, the two FFT passes (two steps each, loads and
+    stores) and the split into R_w and W."""
+    return 8.0 * I * F * F + 96.0 * F * F
+
+
 def timed_runs(eng, vid, mask, blocks, patches, steps, warmup, stream, dev):
     import torch
     for _ in range(warmup):
@@ -256,6 +264,127 @@ def learned_leg(P, vid, mask, blocks, plain_patches, args, stream, dev):
     return out
 
 
+def _crossing(points, target):
+    """points: (iters, ms per step, psnr) in increasing iters.  The time per
+    step at which the curve first reaches PSNR `target`, interpolated linearly
+    in PSNR between the bracketing points; None if it never does."""
+    prev = None
+    for it, ms, ps in points:
+        if ps >= target:
+            if prev is None or prev[2] >= target:
+                return ms, it
+            f = (target - prev[2]) / (ps - prev[2])
+            return prev[1] + f * (ms - prev[1]), prev[0] + f * (it - prev[0])
+        prev = (it, ms, ps)
+    return None
+
+
+def learned_curve(P, vid, mask, blocks, stream, dev, plain_iters=(50, 60, 75, 100, 125, 150, 175, 200),
+                  learned_iters=(25, 50, 75, 100, 150)):
+    """Learned initialisation against plain extrapolation at equal PSNR, on the
+    headline batch: PSNR (lost samples against the frames) and blocks/s of
+    plain extrapolation at each I of plain_iters and of the network followed
+    by k iterations for each k of learned_iters (the network trained for that
+    k -- it supplies what iterations beyond k add -- where one is shipped,
+    else the one trained for k = 50; each point names its network).  The comparison point is
+    plain I=200's PSNR - 0.1 dB: the blocks/s of each curve there
+    (interpolated) and their ratio (learned over plain); and, for every learned
+    point, plain extrapolation at that point's own PSNR and the ratio there."""
+    import torch
+    from paper_2204_14193_gb300 import train_init
+    n = len(blocks)
+    truth = train_init.truth_patches(vid, blocks)
+    ps = lambda p: train_init.psnr(p.view(n, 16, 16), truth)  # noqa: E731
+    pt = torch.empty(n * 256, dtype=torch.float32, device=dev)
+    plain = []
+    for I in plain_iters:
+        eng = P.Engine([dict(CLS, iters=I)])
+        ms = timed_runs(eng, vid, mask, blocks, pt, 3, 2, stream, dev)
+        eng.close()
+        plain.append((I, ms, ps(pt)))
+    learned, nets = [], dict(train_init.shipped_networks())
+    for k in learned_iters:
+        # the network trained for k iterations after it, else the one trained for 50
+        path = nets.get(k, nets.get(50))
+        if path is None:
+            continue
+        eng = P.Engine([CLS], init="learned", init_iters=k, weights=train_init.load_weights(path))
+        ms = timed_runs(eng, vid, mask, blocks, pt, 3, 2, stream, dev)
+        eng.close()
+        learned.append((k, ms, ps(pt), os.path.basename(path)))
+    learned.sort()
+    p200 = dict((it, q) for it, _m, q in plain).get(200)
+    target = p200 - 0.1 if p200 is not None else None
+    lpts = []
+    for k, m, q, net in learned:
+        cp = _crossing(plain, q)      # plain extrapolation at the learned point's own PSNR
+        lpts.append({"init_iters": k, "network": net, "blocks_per_s": n / (m / 1e3), "psnr_db": q,
+                     "plain_at_equal_psnr": None if cp is None else {"iters": cp[1], "blocks_per_s": n / (cp[0] / 1e3)},
+                     "ratio_at_equal_psnr": None if cp is None else cp[0] / m})
+    out = {"plain": [{"iters": it, "blocks_per_s": n / (m / 1e3), "psnr_db": q} for it, m, q in plain],
+           "learned": lpts,
+           "target_psnr_db": target, "target": "plain I=200 PSNR - 0.1 dB"}
+    if target is not None:
+        cp, cl = _crossing(plain, target), _crossing([t[:3] for t in learned], target)
+        out["plain_at_target"] = None if cp is None else {"blocks_per_s": n / (cp[0] / 1e3), "iters": cp[1]}
+        out["learned_at_target"] = None if cl is None else {"blocks_per_s": n / (cl[0] / 1e3), "init_iters": cl[1]}
+        out["ratio_at_equal_psnr"] = (cp[0] / cl[0]) if (cp and cl) else None
+        if learned and cl is None:
+            best = max(learned, key=lambda t: t[2])
+            out["learned_best"] = {"init_iters": best[0], "network": best[3], "psnr_db": best[2],
+                                   "below_target_db": target - best[2], "blocks_per_s": n / (best[1] / 1e3)}
+    return out
+
+
+def oracle_rate(jobs, seconds: float, threads: int):
+    """The FP64 oracle on (image, mask, x, y, class) jobs, `threads` host
+    threads, until about `seconds` of wall time or the jobs are done.
+    Returns (blocks/s, blocks done)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import image as oimage
+    done, t0 = 0, time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while done < len(jobs) and (done == 0 or time.perf_counter() - t0 < seconds):
+            part = jobs[done:done + 4 * threads]
+            list(ex.map(lambda j: oimage.conceal_block(j[0], j[1], j[2], j[3], j[4]), part))
+            done += len(part)
+    return done / (time.perf_counter() - t0), done
+
+
+def small_configs(P, stream, dev, with_oracle: bool, seconds: float):
+    """The two small workloads, device-resident, one graph replay each:
+    one 48x48 FP32 area with a centred 16x16 hole, I=100 (the latency of one
+    block), and a 512x512 8-bit image with 256 non-adjacent 16x16 losses,
+    I=200 (fewer items than the GPU's CTA slots: one wave).  Beside each, the
+    FP64 oracle on the same blocks (one host thread for the single area, all
+    host threads for the 256 blocks)."""
+    import torch
+    from paper_2204_14193_gb300 import synth
+    cores = len(os.sched_getaffinity(0))
+    out = {}
+    img1 = synth.make_image(1, 48, 48, u8=False)[None]
+    b1 = np.array([[0, 16, 16, 0]], np.int32)
+    m1 = synth.loss_mask(b1, [16], 1, 48, 48)
+    img2 = synth.make_image(2, 512, 512)[None]
+    b2 = synth.grid_losses(3, 512, 512, 16, 0.25, non_adjacent=True)
+    m2 = synth.loss_mask(b2, [16], 1, 512, 512)
+    for name, img, bl, mk, I, threads in (("single_area_fp32_i100", img1, b1, m1, 100, 1),
+                                          ("image_512_u8_256_blocks_i200", img2, b2, m2, 200, cores)):
+        cls = dict(CLS, iters=I)
+        eng = P.Engine([cls])
+        dimg, dmask = torch.from_numpy(img).to(dev), torch.from_numpy(mk).to(dev)
+        pt = torch.empty(len(bl) * 256, dtype=torch.float32, device=dev)
+        ms = timed_runs(eng, dimg, dmask, bl, pt, 20, 5, stream, dev)
+        eng.close()
+        r = {"blocks": int(len(bl)), "ms_per_launch": ms, "value": len(bl) / (ms / 1e3), "unit": "blocks/s"}
+        if with_oracle:
+            jobs = [(img[0], mk[0], int(x), int(y), cls) for _, x, y, _c in bl]
+            rate, nd = oracle_rate(jobs * max(1, int(8 * threads // len(jobs))), seconds, threads)
+            r["oracle"] = {"value": rate, "unit": "blocks/s", "threads": threads, "blocks_done": nd, "kind": "oracle"}
+        out[name] = r
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -271,13 +400,13 @@ def iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, peak_gbs):
         eng = P.Engine([dict(CLS, iters=I)])
         ms = timed_runs(eng, vid, mask, blocks, patches, 3, 2, stream, dev)
         eng.close()
-        achieved = n * 8.0 * (I - 1) * CLS["fft"] ** 2 / (ms / 1e3) / 1e9
+        achieved = n * smem_bytes_per_block(CLS["fft"], I) / (ms / 1e3) / 1e9
         out[f"i{I}"] = {"value": n / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms,
                         "smem_frac": achieved / peak_gbs}
     return out
 
 
-def uneven_batch(P, args, stream, dev):
+def uneven_batch(P, args, stream, dev, with_oracle=False, seconds=6.0):
     """30 frames of 1920x1080 u8 video, 3% of the samples lost in mixed
     4x4 / 8x8 / 16x16 blocks (borders 6/12/16, FFT 16/32/64), I = 200, one
     launch over all sizes."""
@@ -295,7 +424,21 @@ def uneven_batch(P, args, stream, dev):
     ms = timed_runs(eng, vid, mask, blocks, pt, 5, 3, stream, dev)
     eng.close()
     counts = np.bincount(blocks[:, 3], minlength=3)
-    return {"value": len(blocks) / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms,
+    oracle_line = None
+    if with_oracle:
+        # the FP64 oracle on a seeded sample of the same blocks, all host threads
+        rng = np.random.default_rng(11)
+        pick = rng.permutation(len(blocks))[:2048]
+        frames = sorted(set(int(blocks[i, 0]) for i in pick))
+        vh = {f: vid[f].cpu().numpy() for f in frames}
+        mh = {f: mask[f].cpu().numpy() for f in frames}
+        jobs = [(vh[int(blocks[i, 0])], mh[int(blocks[i, 0])], int(blocks[i, 1]), int(blocks[i, 2]),
+                 classes[int(blocks[i, 3])]) for i in pick]
+        cores = len(os.sched_getaffinity(0))
+        rate, nd = oracle_rate(jobs, seconds, cores)
+        oracle_line = {"value": rate, "unit": "blocks/s", "threads": cores, "blocks_done": nd, "kind": "oracle",
+                       "sample": "seeded sample of the batch's blocks (all three sizes)"}
+    return {"value": len(blocks) / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms, "oracle": oracle_line,
             "workload": f"{T3} x {W3}x{H3} u8 frames, 3% of samples lost in 4/8/16 blocks "
                         f"({counts[0]}/{counts[1]}/{counts[2]}), F 16/32/64, I=200, one launch",
             "blocks": int(len(blocks))}
@@ -325,7 +468,7 @@ def video_volumes(P, args, stream, dev, peak_gbs):
         eng.close()
         mse = float(((pt.view(-1, b, b).clamp(0, 255) - truth) ** 2).mean())
         bins = 32 * 32 * (4 if frames else 1)
-        achieved = len(blocks) * 8.0 * 199 * bins / (ms / 1e3) / 1e9
+        achieved = len(blocks) * (8.0 * 200 * bins + 96.0 * bins) / (ms / 1e3) / 1e9
         out[name] = {"value": len(blocks) / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms,
                      "psnr_db": 10 * np.log10(255.0 ** 2 / max(mse, 1e-12)), "smem_frac": achieved / peak_gbs}
     return out
@@ -472,34 +615,49 @@ def main():
         # the e2e patches equal the device-path patches bit for bit
         assert np.array_equal(h_patch, patches.cpu().numpy()), "host entry point disagrees with device path"
 
-    learned = None
-    if not args.no_learned and args.iters == 200:
-        learned = learned_leg(P, vid, mask, blocks, patches, args, stream, dev)
-    props0 = torch.cuda.get_device_properties(dev)
-    sm_mhz0 = clocks["sm_mhz"] or clocks["sm_max_mhz"] or max_sm_clock_mhz(local)
-    peak0 = props0.multi_processor_count * 128.0 * sm_mhz0 * 1e6 / 1e9
-    sweep = uneven = video = ordered = None
-    if not args.no_extra and args.iters == 200:
-        ordered = ordered_leg(P, vid, mask, blocks, patches, stream, dev)
-        sweep = iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, peak0)
-        uneven = uneven_batch(P, args, stream, dev)
-        video = video_volumes(P, args, stream, dev, peak0)
-
-    # ---- roofline of the persistent kernel (shared-memory bound) ----
+    # the shared-memory peak: measured on this GPU (a stream of conflict-free
+    # 16-byte shared loads on every SM), right after the timed region
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    F, I = cls["fft"], cls["iters"]
-    smem_bytes_block = 8.0 * max(I - 1, 0) * F * F          # W reads of the residual updates
-    flops_block = I * F * F * 11.0 + 3 * 5.0 * F * F * np.log2(F * F)
     sm_mhz = clocks["sm_mhz"] or clocks["sm_max_mhz"] or max_sm_clock_mhz(local)
+    derived_peak = sms * 128.0 * sm_mhz * 1e6 / 1e9
+    try:
+        smem_peak = P.fse_measure_smem_bandwidth(local)
+        peak_basis = (f"measured: conflict-free 16-byte shared-memory load stream on all {sms} SMs "
+                      f"(fse_measure_smem_bandwidth, best of 5), {smem_peak / (sms * sm_mhz * 1e6 / 1e9):.1f} B/clk "
+                      f"per SM at the {sm_mhz:.0f} MHz median SM clock of the timed region (derived 128 B/clk: "
+                      f"{derived_peak:.0f} GB/s)")
+    except P.FseError:
+        smem_peak = derived_peak
+        peak_basis = f"derived: {sms} SMs x 128 B/clk x {sm_mhz:.0f} MHz (the measurement failed)"
+
+    learned = curve = None
+    if not args.no_learned and args.iters == 200:
+        learned = learned_leg(P, vid, mask, blocks, patches, args, stream, dev)
+        curve = learned_curve(P, vid, mask, blocks, stream, dev)
+    sweep = uneven = video = ordered = small = None
+    if not args.no_extra and args.iters == 200:
+        ordered = ordered_leg(P, vid, mask, blocks, patches, stream, dev)
+        sweep = iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, smem_peak)
+        uneven = uneven_batch(P, args, stream, dev, with_oracle=rank == 0 and not args.no_cpu_baseline,
+                              seconds=args.cpu_seconds / 2)
+        video = video_volumes(P, args, stream, dev, smem_peak)
+        small = small_configs(P, stream, dev, with_oracle=rank == 0 and not args.no_cpu_baseline,
+                              seconds=args.cpu_seconds / 4)
+
+    # ---- roofline of the persistent kernel (shared-memory bound) ----
+    F, I = cls["fft"], cls["iters"]
+    smem_bytes_block = smem_bytes_per_block(F, I)
+    flops_block = I * F * F * 11.0 + 3 * 5.0 * F * F * np.log2(F * F)
     achieved = n_blocks * smem_bytes_block / (ms / 1e3) / 1e9
-    peak = sms * 128.0 * sm_mhz * 1e6 / 1e9
+    peak = smem_peak
     fp32_peak = sms * 256.0 * sm_mhz * 1e6 / 1e12
     traffic = profile_traffic()
     roofline = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_basis": f"{sms} SMs x 128 B/clk shared-memory bandwidth x {sm_mhz:.0f} MHz median SM "
-                              "clock under load (derived, no measured smem peak exists)",
+                "traffic": traffic, "bytes_per_block": smem_bytes_block,
+                "bytes_basis": "8 I F^2 (one 8-byte W operand per bin and iteration) + 96 F^2 (the FFT passes, "
+                               "the weighting and the split: twelve 8-byte sweeps of the F x F grid)",
+                "peak_basis": peak_basis,
                 "fp32": {"achieved_tflops": n_blocks * flops_block / (ms / 1e3) / 1e12,
                          "peak_tflops": fp32_peak,
                          "frac": n_blocks * flops_block / (ms / 1e3) / 1e12 / fp32_peak}}
@@ -528,8 +686,9 @@ def main():
                            "l2": f"inputs larger than L2 (frames + mask = {2 * frames * H * W / 1e6:.0f} MB per GPU, "
                                  "L2 129 MB)"},
                 "clocks": clocks, "gpu_launches": args.steps, "roofline": roofline,
-                "e2e": e2e, "cpu_baseline": cpu, "learned_init": learned, "iteration_sweep": sweep,
-                "uneven_batch": uneven, "video_volumes": video, "ordered": ordered}
+                "e2e": e2e, "cpu_baseline": cpu, "learned_init": learned, "learned_vs_plain": curve,
+                "iteration_sweep": sweep, "uneven_batch": uneven, "video_volumes": video, "ordered": ordered,
+                "small_configs": small}
         print(json.dumps(line))
     eng.close()
     if world > 1:

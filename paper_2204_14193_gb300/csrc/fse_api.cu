@@ -82,7 +82,7 @@ struct fse_handle {
     fse_config cfg{};
     int device = 0;
     int sm_count = 0;
-    int max_ctas[3][2] = {};       // CTAs per SM of each kernel set (fse_device.cuh) x {128, 256} threads
+    int max_ctas[4][2] = {};       // CTAs per SM of each kernel set (fse_device.cuh) x {128, 256} threads
     size_t smem_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     float *d_wtab[FSE_MAX_CLASSES] = {};
@@ -346,8 +346,7 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         const fse_class &k = cfg.cls[pl.seg_cls[sg]];
         all_f64 = all_f64 && k.fft == 64 && k.frames <= 1;
     }
-    // traced batches record the top-two gap, which the FFT-64 set leaves out
-    pl.ks = fse::kernel_set_for(h->ext, all_f64 && !(cfg.flags & FSE_FLAG_TRACE));
+    pl.ks = fse::kernel_set_for(h->ext, all_f64, (cfg.flags & FSE_FLAG_TRACE) != 0);
     return FSE_OK;
 }
 
@@ -1072,12 +1071,14 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     h->smem_bytes = smem;
     h->ext = (cfg->flags & FSE_FLAG_ORDERED) != 0;
     for (int c = 0; c < cfg->n_classes; ++c) h->ext = h->ext || cfg->cls[c].frames > 1;
-    // the kernel sets this handle's batches can run: the extended set, or the
-    // image set and (with an FFT-64 class) the FFT-64 set
+    // the kernel sets this handle's batches can run: the traced set, the
+    // extended set, or the image set and (with an FFT-64 class) the FFT-64 set
     bool any64 = false;
     for (int c = 0; c < cfg->n_classes; ++c) any64 = any64 || cfg->cls[c].fft == 64;
-    for (int ks : {fse::kSetImage, fse::kSetExt, fse::kSetF64}) {
-        if ((ks == fse::kSetExt) != h->ext || (ks == fse::kSetF64 && !any64)) continue;
+    const bool traced = (cfg->flags & FSE_FLAG_TRACE) != 0;
+    for (int ks : {fse::kSetImage, fse::kSetExt, fse::kSetF64, fse::kSetTrace}) {
+        if (traced != (ks == fse::kSetTrace)) continue;
+        if (!traced && ((ks == fse::kSetExt) != h->ext || (ks == fse::kSetF64 && !any64))) continue;
         for (int t = 0; t < 2; ++t) {
             int occ = 0;
             CREATE_CUDA(fse::batch_kernel_prepare(ks, t ? 256 : 128, smem, &occ));

@@ -234,7 +234,7 @@ __host__ __device__ constexpr int cta_region_bytes(int F) { return F == 64 ? 16 
 constexpr int kMaxWarps = 8;
 
 // kernel sets of fse_batch_kernel (see there)
-constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2;
+constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2, kSetTrace = 3;
 
 struct RedShared {
     uint4 win[2][kMaxWarps];   // per-warp argmax candidates, double-buffered by iteration parity
@@ -599,7 +599,7 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 // ------------------------------------------------------- per-block worker
 // NP: B samples per thread (compile time; the caller picks the smallest
 // variant that covers b*b).  EXT: built with ordered concealment.
-template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false>
+template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false, bool TMA = false>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh, uint32_t &tph) {
     using G = Geo<F, PAIRS>;
@@ -645,7 +645,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     constexpr int NPOS = F * F / TB;
     float sv[NPOS];
     uint8_t mk[NPOS];
-    if (G::RUNS && P.tma) {
+    if (TMA && G::RUNS && P.tma) {
         // 8-bit F = 64 windows: the image and mask tiles of the M x M area
         // arrive in shared memory by two TMA copies.  The tile's first column
         // is the area's first column rounded down to a 16-byte boundary (xs
@@ -1208,7 +1208,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     }
 }
 
-template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false, bool GAP = false>
+template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false, bool GAP = false, bool TMA = false>
 __device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
                                               unsigned char *smem, const float2 *s_tw, RedShared *rsh,
                                               uint32_t &tph) {
@@ -1216,8 +1216,8 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
     if constexpr (FT == 1) {
         constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
         constexpr int NPL = PAIRS / 2;                // covers b <= F/2
-        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT, GAP>(P, C, first, count, smem, s_tw, rsh, tph);
-        else process<F, PAIRS, NT, NPL, EXT, GAP>(P, C, first, count, smem, s_tw, rsh, tph);
+        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT, GAP, TMA>(P, C, first, count, smem, s_tw, rsh, tph);
+        else process<F, PAIRS, NT, NPL, EXT, GAP, TMA>(P, C, first, count, smem, s_tw, rsh, tph);
     } else {
         // a volume's block group is FT times larger: b <= F/2 needs
         // F^2/4 / TB = PAIRS / (2 FT) samples per thread (at least 1)
@@ -1231,20 +1231,22 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
 // most three CTAs per SM.  KS selects what the instantiation carries:
 //   kSetImage  image classes of every FFT size (16, 32, 64)
 //   kSetExt    also video volumes and ordered concealment
-//   kSetF64    image classes of FFT size 64 only, without the trace's
-//              top-two gap (traced batches run kSetImage)
+//   kSetF64    image classes of FFT size 64 only
+//   kSetTrace  everything kSetExt runs, plus the trace's top-two gap (the
+//              largest energy besides each pick): traced batches only
 // A batch runs the smallest set that covers its classes, so the code and
 // register allocation of the common cases are not burdened by the others.
 template <int NT, int KS>
 __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant__ DevParams P) {
     constexpr int PAIRS = 2048 / NT;
-    constexpr bool EXT = KS == kSetExt;
+    constexpr bool EXT = KS == kSetExt || KS == kSetTrace;
+    constexpr bool GAP = KS == kSetTrace;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ float2 s_tw[64];
     __shared__ int s_item;
     __shared__ RedShared rsh;
     for (int i = threadIdx.x; i < 64; i += NT) s_tw[i] = P.tw[i];
-    if (threadIdx.x == 0 && P.tma) mbar_init(&rsh.mbar, 1);
+    if (KS == kSetF64 && threadIdx.x == 0 && P.tma) mbar_init(&rsh.mbar, 1);
     uint32_t tph = 0;   // phase of rsh.mbar the next window waits for
     __syncthreads();
     for (;;) {
@@ -1260,16 +1262,16 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
         const int count = min(C.bpi, P.seg_block_start[sg] + P.seg_block_count[sg] - first);
         if (EXT && C.FT == 4) {
             if constexpr (EXT) {
-                if (C.F == 32) process_class<32, PAIRS, NT, 4, true, true>(P, C, first, count, smem, s_tw, &rsh, tph);
-                else process_class<16, PAIRS, NT, 4, true, true>(P, C, first, count, smem, s_tw, &rsh, tph);
+                if (C.F == 32) process_class<32, PAIRS, NT, 4, true, GAP>(P, C, first, count, smem, s_tw, &rsh, tph);
+                else process_class<16, PAIRS, NT, 4, true, GAP>(P, C, first, count, smem, s_tw, &rsh, tph);
             }
         } else if constexpr (KS == kSetF64) {
-            process_class<64, PAIRS, NT, 1, false>(P, C, first, count, smem, s_tw, &rsh, tph);
+            process_class<64, PAIRS, NT, 1, false, false, true>(P, C, first, count, smem, s_tw, &rsh, tph);
         } else {
             switch (C.F) {
-                case 64: process_class<64, PAIRS, NT, 1, EXT, true>(P, C, first, count, smem, s_tw, &rsh, tph); break;
-                case 32: process_class<32, PAIRS, NT, 1, EXT, true>(P, C, first, count, smem, s_tw, &rsh, tph); break;
-                default: process_class<16, PAIRS, NT, 1, EXT, true>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                case 64: process_class<64, PAIRS, NT, 1, EXT, GAP>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                case 32: process_class<32, PAIRS, NT, 1, EXT, GAP>(P, C, first, count, smem, s_tw, &rsh, tph); break;
+                default: process_class<16, PAIRS, NT, 1, EXT, GAP>(P, C, first, count, smem, s_tw, &rsh, tph); break;
             }
         }
         __syncthreads();

@@ -1,0 +1,24 @@
+// fse_kernel_ext.cu -- the persistent concealment kernel for video volumes and
+// ordered concealment as well, 128 threads per CTA (the 256-thread
+// instantiation is in fse_kernel_trace256.cu: the two compile in parallel).
+#include "fse_kernels.cuh"
+
+namespace fse {
+
+template <int NT>
+static cudaError_t prepare_nt(size_t smem, int *ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(fse_batch_kernel<NT, kSetTrace>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fse_batch_kernel<NT, kSetTrace>, NT, smem);
+}
+
+cudaError_t batch_kernel_prepare_trace(int nt, size_t smem, int *ctas_per_sm) {
+    return nt == 256 ? batch_kernel_prepare_trace256(smem, ctas_per_sm) : prepare_nt<128>(smem, ctas_per_sm);
+}
+
+cudaError_t batch_kernel_launch_trace(int nt, int grid, size_t smem, cudaStream_t s, const DevParams &P) {
+    if (nt == 256) return batch_kernel_launch_trace256(grid, smem, s, P);
+    fse_batch_kernel<128, kSetTrace><<<grid, 128, smem, s>>>(P);
+    return cudaGetLastError();
+}
+}  // namespace fse
