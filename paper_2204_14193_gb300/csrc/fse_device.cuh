@@ -486,8 +486,8 @@ __device__ __forceinline__ void quartet_max(int j, float qj, float &tmax, int &j
 // so the reduction is built from as few DEPENDENT such steps as possible:
 // one redux.sync for the max, the owner's register search, one redux.sync for
 // the smallest index, and (multi-warp groups) one shared-memory exchange.
-// GAP (compiled in) and gap (at run time): also the largest energy of the
-// other bins, for the trace's top-two gap.
+// GAP (compiled in: the traced kernel set) and gap (at run time): also the
+// largest energy of the other bins, for the trace's top-two gap.
 template <int F, int PAIRS, int NT, int FT = 1, bool GAP = false>
 __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t *Rim, float tmax, int jb,
                                              const Grp &gr, RedShared *rs, int parity, bool gap = false) {
@@ -598,7 +598,9 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 
 // ------------------------------------------------------- per-block worker
 // NP: B samples per thread (compile time; the caller picks the smallest
-// variant that covers b*b).  EXT: built with ordered concealment.
+// variant that covers b*b).  EXT: built with ordered concealment.  GAP: the
+// traced kernel set (selection trace with the top-two gap; other sets write
+// no trace).  TMA: the FFT-64 set (windows of 8-bit images by TMA).
 template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false, bool TMA = false>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh, uint32_t &tph) {
@@ -824,12 +826,12 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         // ---- S6/S7: coefficient and model ----
         const float cr = pick.rr * cg, ci = pick.ri * cg;
         const int u = (int)(pick.idx / F), v = (int)(pick.idx % F);
-        if (P.tr_sel != nullptr && lt == 0) {
+        if (GAP && P.tr_sel != nullptr && lt == 0) {   // traced launches (their own kernel set)
             const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
             P.tr_sel[o] = (int)pick.idx;
             P.tr_energy[o] = __uint_as_float(pick.ebits);
             P.tr_coef[o] = make_float2(cr, ci);
-            if (GAP && P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
+            if (P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
         }
         // model update of this selection, evaluated on B: g += c phi_(u,v)
         // (independent of the residual update and of the next reduction)
@@ -1114,12 +1116,12 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         const int wt = FT == 1 ? 0 : (int)(pick.idx / (F * F));   // temporal frequency
         // the temporal part of the phase on B's plane, in 64ths of a turn
         const int tphase = FT == 1 ? 0 : (wt * (C.toff + C.tc) * (64 / FT)) & 63;
-        if (P.tr_sel != nullptr && lt == 0) {
+        if (GAP && P.tr_sel != nullptr && lt == 0) {   // traced launches (their own kernel set)
             const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
             P.tr_sel[o] = (int)pick.idx;
             P.tr_energy[o] = __uint_as_float(pick.ebits);
             P.tr_coef[o] = make_float2(cr, ci);
-            if (GAP && P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
+            if (P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
         }
         // model update of this selection, evaluated on B: g += c phi_(u,v)
         // (independent of the residual update and of the next reduction)
