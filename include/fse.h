@@ -161,7 +161,10 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg);
  * At least one of out, patches must be non-NULL when n_blocks > 0.
  * n_blocks == 0 is valid and enqueues nothing.  The batch runs as one
  * persistent, graph-captured launch; the graph is rebuilt only when the block
- * list or a pointer changes.
+ * list or a pointer changes.  The launch shape (threads per CTA, CTAs per SM)
+ * is chosen by timing the candidates on the batch itself the first time a
+ * class mix of that size appears in the process: that first call waits for
+ * its timing runs; later calls and other handles reuse the choice.
  */
 fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, int n_images,
                                  int height, int width, size_t pitch_bytes,

@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -82,6 +83,7 @@ struct fse_handle {
     fse_config cfg{};
     int device = 0;
     int sm_count = 0;
+    int cc = 0;                    // compute capability, major * 10 + minor
     int max_ctas[4][2] = {};       // CTAs per SM of each kernel set (fse_device.cuh) x {128, 256} threads
     size_t smem_bytes = 0;
     cudaStream_t cap_stream = nullptr;
@@ -244,7 +246,8 @@ struct Plan {
     int seg_block_count[FSE_MAX_CLASSES] = {};
     int total_items = 0;
     long long patch_total = 0;
-    uint64_t mix_sig = 0;
+    uint64_t mix_sig = 0;      // class mix of the batch (per handle: class indices)
+    uint64_t tune_key = 0;     // the same by class parameters, for the process-wide tuning cache
     int ks = fse::kSetImage;   // kernel set that covers the batch's classes
 };
 
@@ -333,12 +336,15 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         r.pad = 0;
         pl.sorted[fillp[bk.cls]++] = r;
     }
-    uint64_t sig = 1469598103934665603ull;
+    uint64_t sig = 1469598103934665603ull, tkey = 1469598103934665603ull;
     for (int s = 0; s < pl.n_seg; ++s) {
         const int c = pl.seg_cls[s];
         const int bucket = 32 - __builtin_clz((unsigned)pl.seg_block_count[s]);  // log2 size bucket
         const int key[3] = {c, bucket, cfg.cls[c].iters};
         sig = fnv1a(key, sizeof key, sig);
+        const fse_class &k = cfg.cls[c];
+        const int tk[6] = {k.fft, k.block, k.border, k.frames, k.iters, bucket};
+        tkey = fnv1a(tk, sizeof tk, tkey);
     }
     pl.mix_sig = sig;
     bool all_f64 = true;
@@ -347,6 +353,9 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         all_f64 = all_f64 && k.fft == 64 && k.frames <= 1;
     }
     pl.ks = fse::kernel_set_for(h->ext, all_f64, (cfg.flags & FSE_FLAG_TRACE) != 0);
+    const long long dev_key[5] = {pl.ks, h->sm_count, h->cc, (long long)h->smem_bytes,
+                                  (long long)(cfg.flags & FSE_FLAG_ORDERED)};
+    pl.tune_key = fnv1a(dev_key, sizeof dev_key, tkey);
     return FSE_OK;
 }
 
@@ -576,10 +585,18 @@ fse_status capture_graph(fse_handle *h, int ks, int nt, int grid, cudaGraphExec_
     return FSE_OK;
 }
 
+// Choices of the autotuner shared by every handle of the process: the same
+// class mix (by class parameters and batch-size bucket) on the same kind of
+// device with the same kernel set is not timed again by a new handle.
+std::mutex g_tune_mu;
+std::unordered_map<uint64_t, std::pair<int, int>> g_tuned;
+
 // Autotuner: time each candidate mapping -- 128 threads per CTA (32 bins per
-// thread) or 256 (16 bins per thread), 1..3 CTAs per SM -- on the actual
-// batch (the outputs are identical for every candidate, so the runs are
-// harmless) and keep the fastest per class-mix signature.
+// thread) or 256 (16 bins per thread), the two largest CTA counts per SM --
+// on the actual batch (the outputs are identical for every candidate, so the
+// runs are harmless) and keep the fastest per class mix, in the handle and
+// in the process-wide cache.  The first call with a new class mix waits for
+// its timing runs; later calls (and other handles) reuse the choice.
 fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *best_nt, int *best_cps) {
     for (auto &kv : h->tuned)
         if (kv.first == pl.mix_sig) {
@@ -587,6 +604,16 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
             *best_cps = kv.second.second;
             return FSE_OK;
         }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(pl.tune_key);
+        if (it != g_tuned.end()) {
+            h->tuned.emplace_back(pl.mix_sig, it->second);
+            *best_nt = it->second.first;
+            *best_cps = it->second.second;
+            return FSE_OK;
+        }
+    }
     int bnt = 256, bcps = ctas_per_sm(h, pl.ks, 256);
     // small batches cannot fill the machine: no measurement needed
     if ((long long)pl.total_items >= 2LL * h->sm_count) {
@@ -621,6 +648,10 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
         cudaEventDestroy(e1);
     }
     h->tuned.emplace_back(pl.mix_sig, std::make_pair(bnt, bcps));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[pl.tune_key] = std::make_pair(bnt, bcps);
+    }
     *best_nt = bnt;
     *best_cps = bcps;
     return FSE_OK;
@@ -1062,6 +1093,7 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     cudaDeviceProp prop;
     CREATE_CUDA(cudaGetDeviceProperties(&prop, h->device));
     h->sm_count = prop.multiProcessorCount;
+    h->cc = prop.major * 10 + prop.minor;
     // dynamic smem: the largest per-item region over the configured classes
     size_t smem = 0;
     for (int c = 0; c < cfg->n_classes; ++c) {

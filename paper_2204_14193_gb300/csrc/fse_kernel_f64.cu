@@ -1,11 +1,14 @@
-// fse_kernel_f64.cu -- the persistent concealment kernel for image classes of FFT size 64 only (the paper's 48 x 48 areas in a 64 x 64 FFT), 128 and 256 threads per CTA.
+// fse_kernel_f64.cu -- the persistent concealment kernel for image classes of
+// FFT size 64 only (the paper's 48 x 48 areas in a 64 x 64 FFT), 128 and 256
+// threads per CTA.
 #include "fse_kernels.cuh"
 
 namespace fse {
 
 template <int NT>
 static cudaError_t prepare_nt(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fse_batch_kernel<NT, kSetF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(fse_batch_kernel<NT, kSetF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fse_batch_kernel<NT, kSetF64>, NT, smem);
 }

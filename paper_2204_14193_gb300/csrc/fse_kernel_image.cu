@@ -1,11 +1,14 @@
-// fse_kernel_image.cu -- the persistent concealment kernel for image classes of every FFT size, 128 and 256 threads per CTA.
+// fse_kernel_image.cu -- the persistent concealment kernel for image classes of
+// every FFT size, 128 and 256 threads per CTA; the dispatch over the kernel
+// sets.
 #include "fse_kernels.cuh"
 
 namespace fse {
 
 template <int NT>
 static cudaError_t prepare_nt(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fse_batch_kernel<NT, kSetImage>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(fse_batch_kernel<NT, kSetImage>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fse_batch_kernel<NT, kSetImage>, NT, smem);
 }

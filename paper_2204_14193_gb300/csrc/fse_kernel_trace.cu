@@ -7,7 +7,8 @@ namespace fse {
 
 template <int NT>
 static cudaError_t prepare_nt(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fse_batch_kernel<NT, kSetTrace>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(fse_batch_kernel<NT, kSetTrace>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fse_batch_kernel<NT, kSetTrace>, NT, smem);
 }

@@ -5,7 +5,8 @@
 namespace fse {
 
 cudaError_t batch_kernel_prepare_trace256(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fse_batch_kernel<256, kSetTrace>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(fse_batch_kernel<256, kSetTrace>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fse_batch_kernel<256, kSetTrace>, 256, smem);
 }
