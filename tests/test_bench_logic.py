@@ -32,7 +32,7 @@ def test_crossing_takes_the_first_crossing_of_a_non_monotonic_curve():
 
 
 def test_shared_memory_bytes_per_block():
-    # the survey's 8 I F^2 + ~0.4 MB at F = 64, I = 200 (about 7.0 MB)
+    # 8 I F^2 plus about 0.4 MB of FFT passes at F = 64, I = 200 (about 7.0 MB)
     assert bench.smem_bytes_per_block(64, 200) == 8 * 200 * 4096 + 96 * 4096
     assert bench.smem_bytes_per_block(64, 200) == pytest.approx(6.95e6, rel=1e-3)
     assert bench.smem_bytes_per_block(32, 0) == 96 * 1024
