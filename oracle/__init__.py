@@ -55,6 +55,10 @@ def _load():
             lib.oracle_weight.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, u8p, dp]
             lib.oracle_cfse.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double, ctypes.c_int,
                                         ip, ip, dp, dp, dp, dp, dp, dp, dp]
+            lib.oracle_cfse_fixw.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ip, ip, dp, dp, dp, dp, dp, dp, dp]
+            lib.oracle_fix_code.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.oracle_fix_code.restype = ctypes.c_int
             lib.oracle_cfse_spatial.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double,
                                                 ctypes.c_int, ip, dp, dp, dp]
             lib.oracle_fft3.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
@@ -63,7 +67,7 @@ def _load():
                                          ip, ip, dp, dp, dp, dp]
             lib.oracle_cfse3_spatial.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_double,
                                                  ctypes.c_int, ip, dp, dp]
-            for name in ("oracle_fft2", "oracle_cfse", "oracle_cfse_spatial", "oracle_fft3", "oracle_cfse3",
+            for name in ("oracle_fft2", "oracle_cfse", "oracle_cfse_fixw", "oracle_cfse_spatial", "oracle_fft3", "oracle_cfse3",
                          "oracle_cfse3_spatial"):
                 getattr(lib, name).restype = ctypes.c_int
             if hasattr(lib, "oracle_conv3x3_fwd"):
@@ -135,8 +139,15 @@ class CfseResult:
         self.W = W                # complex[F,F] spectrum of w
 
 
+def fix_code(x: float, W00: float) -> int:
+    """16-bit fixed-point code of a spectrum value x of W: x / W[0,0] in units
+    of 1/32767, rounded to nearest (ties to even, decided in FP32), held to
+    [-32767, 32767].  The code stands for code * W00 / 32767."""
+    return int(_load().oracle_fix_code(float(x), float(W00)))
+
+
 def cfse(s: np.ndarray, w: np.ndarray, gamma: float, iters: int,
-         forced: np.ndarray | None = None) -> CfseResult:
+         forced: np.ndarray | None = None, wfix_from: int | None = None) -> CfseResult:
     """Algorithm 1 on an F x F grid (w real, 0 off the support area; s real or
     complex).
 
@@ -144,6 +155,10 @@ def cfse(s: np.ndarray, w: np.ndarray, gamma: float, iters: int,
     (guided replay); the recorded energies still describe the oracle's own
     residual at that point, so callers can check that each forced pick is an
     epsilon-argmax.
+
+    ``wfix_from`` = K makes the residual updates of iterations K, K+1, ...
+    (0-based) read W in 16-bit fixed point (``fix_code``; reduced-precision
+    residual storage); None keeps every update in FP64.
     """
     s_re, s_im = _split(s)
     w = np.ascontiguousarray(w, dtype=np.float64)
@@ -162,10 +177,16 @@ def cfse(s: np.ndarray, w: np.ndarray, gamma: float, iters: int,
     if forced is not None:
         fp = np.ascontiguousarray(forced, dtype=np.int32)
         assert fp.shape[0] >= I
-    rc = _load().oracle_cfse(F, _ptr(s_re), _ptr(s_im), _ptr(w), float(gamma), I,
-                             _ptr(fp, ctypes.c_int32),
-                             _ptr(sel, ctypes.c_int32), _ptr(coef), _ptr(e_sel), _ptr(e_max),
-                             _ptr(e_sec), _ptr(g), _ptr(R), _ptr(W))
+    if wfix_from is None:
+        rc = _load().oracle_cfse(F, _ptr(s_re), _ptr(s_im), _ptr(w), float(gamma), I,
+                                 _ptr(fp, ctypes.c_int32),
+                                 _ptr(sel, ctypes.c_int32), _ptr(coef), _ptr(e_sel), _ptr(e_max),
+                                 _ptr(e_sec), _ptr(g), _ptr(R), _ptr(W))
+    else:
+        rc = _load().oracle_cfse_fixw(F, _ptr(s_re), _ptr(s_im), _ptr(w), float(gamma), I,
+                                      max(0, int(wfix_from)), _ptr(fp, ctypes.c_int32),
+                                      _ptr(sel, ctypes.c_int32), _ptr(coef), _ptr(e_sel),
+                                      _ptr(e_max), _ptr(e_sec), _ptr(g), _ptr(R), _ptr(W))
     if rc != 0:
         raise ValueError("oracle_cfse: bad argument")
     cplx = lambda a: (a[0::2] + 1j * a[1::2]).reshape(F, F)  # noqa: E731

@@ -130,10 +130,49 @@ void oracle_weight(int M, int N, double rho, const uint8_t *support, double *w)
  *   W_out[2F^2]   the spectrum W of w.
  * Returns 0, or -1 on a bad argument.
  */
+int oracle_cfse_fixw(int F, const double *s, const double *s_im, const double *w,
+                     double gamma, int iters, int wfix_from, const int32_t *forced, int32_t *sel,
+                     double *coef, double *e_sel, double *e_max, double *e_second,
+                     double *g, double *R_out, double *W_out);
+
 int oracle_cfse(int F, const double *s, const double *s_im, const double *w,
                 double gamma, int iters, const int32_t *forced, int32_t *sel, double *coef,
                 double *e_sel, double *e_max, double *e_second,
                 double *g, double *R_out, double *W_out)
+{
+    return oracle_cfse_fixw(F, s, s_im, w, gamma, iters, iters, forced, sel, coef, e_sel, e_max,
+                            e_second, g, R_out, W_out);
+}
+
+/* The 16-bit fixed-point code of a spectrum value x of W: x / W[0,0] in
+ * units of 1/32767, rounded to the nearest integer (ties to even) and held
+ * to [-32767, 32767].  |W[k,l]| <= W[0,0] for a non-negative weight, so the
+ * codes cover W without overflow.  The rounding decision is taken in FP32
+ * (x and 1 / W[0,0] rounded to FP32, their product with 32767 rounded to
+ * FP32), the precision in which the reduced-precision kernel decides it;
+ * the value a code stands for, code W[0,0] / 32767, is FP64. */
+int oracle_fix_code(double x, double W00)
+{
+    float rinv = 1.0f / (float)W00;
+    float qs = 32767.0f * rinv;
+    float t = (float)x * qs;
+    double c = nearbyint((double)t);   /* default rounding mode: to nearest, ties to even */
+    if (c > 32767.0) c = 32767.0;
+    if (c < -32767.0) c = -32767.0;
+    return (int)c;
+}
+
+/*
+ * Algorithm 1 with reduced-precision residual storage: as oracle_cfse, but
+ * the updates of iterations nu >= wfix_from (0-based) read W in 16-bit fixed
+ * point (each real and imaginary part replaced by the value of its code,
+ * oracle_fix_code; everything else stays FP64, and c-hat still divides by
+ * the exact W[0,0]).  wfix_from >= iters is oracle_cfse itself.
+ */
+int oracle_cfse_fixw(int F, const double *s, const double *s_im, const double *w,
+                     double gamma, int iters, int wfix_from, const int32_t *forced, int32_t *sel,
+                     double *coef, double *e_sel, double *e_max, double *e_second,
+                     double *g, double *R_out, double *W_out)
 {
     if (!is_pow2(F) || iters < 0) return -1;
     long P = (long)F * F;
@@ -154,6 +193,20 @@ int oracle_cfse(int F, const double *s, const double *s_im, const double *w,
     oracle_fft2(F, Wr, Wi, -1);
     int have_support = Wr[0] > 0.0;
     double W0bar = have_support ? 1.0 / Wr[0] : 0.0;
+    /* the fixed-point W read by the updates from iteration wfix_from on */
+    double *Hr = NULL, *Hi = NULL;
+    if (wfix_from < iters && have_support) {
+        Hr = malloc(P * sizeof(double));
+        Hi = malloc(P * sizeof(double));
+        if (!Hr || !Hi) {
+            free(Hr); free(Hi); free(Rr); free(Ri); free(Wr); free(Wi); free(Gr); free(Gi);
+            return -1;
+        }
+        for (long p = 0; p < P; ++p) {
+            Hr[p] = oracle_fix_code(Wr[p], Wr[0]) * Wr[0] / 32767.0;
+            Hi[p] = oracle_fix_code(Wi[p], Wr[0]) * Wr[0] / 32767.0;
+        }
+    }
 
     for (int nu = 0; nu < iters; ++nu) {
         /* basis function selection: argmax |R_w|^2, ties -> smallest index */
@@ -184,10 +237,11 @@ int oracle_cfse(int F, const double *s, const double *s_im, const double *w,
         Gr[pick] += (double)P * cr;
         Gi[pick] += (double)P * ci;
         /* residual update: R_w[k,l] -= c W[k-u, l-v] (indices modulo F) */
+        const double *Ur = (Hr && nu >= wfix_from) ? Hr : Wr, *Ui = (Hr && nu >= wfix_from) ? Hi : Wi;
         for (int k = 0; k < F; ++k)
             for (int l = 0; l < F; ++l) {
                 long q = (long)(((k - u) % F + F) % F) * F + (((l - v) % F + F) % F);
-                double wr = Wr[q], wi = Wi[q];
+                double wr = Ur[q], wi = Ui[q];
                 Rr[(long)k * F + l] -= cr * wr - ci * wi;
                 Ri[(long)k * F + l] -= cr * wi + ci * wr;
             }
@@ -199,7 +253,7 @@ int oracle_cfse(int F, const double *s, const double *s_im, const double *w,
     }
     if (R_out) for (long p = 0; p < P; ++p) { R_out[2 * p] = Rr[p]; R_out[2 * p + 1] = Ri[p]; }
     if (W_out) for (long p = 0; p < P; ++p) { W_out[2 * p] = Wr[p]; W_out[2 * p + 1] = Wi[p]; }
-    free(Rr); free(Ri); free(Wr); free(Wi); free(Gr); free(Gi);
+    free(Rr); free(Ri); free(Wr); free(Wi); free(Gr); free(Gi); free(Hr); free(Hi);
     return 0;
 }
 

@@ -85,24 +85,28 @@ def conceal_block_init(img, mask, x, y, cls, est, forced=None):
     return patch, res
 
 
-def conceal_block(img, mask, x, y, cls, forced=None):
-    """Run the oracle on one block; returns (patch b x b, CfseResult)."""
+def conceal_block(img, mask, x, y, cls, forced=None, wfix_from=None):
+    """Run the oracle on one block; returns (patch b x b, CfseResult).
+    wfix_from: reduced-precision residual storage from that iteration on
+    (``oracle.cfse``)."""
     b, d, F, rho, gamma, iters = (cls["block"], cls["border"], cls["fft"], cls["rho"],
                                   cls["gamma"], cls["iters"])
     s_grid, w_grid, off = area_inputs(img, mask, x, y, b, d, F, rho)
-    res = cfse(s_grid, w_grid, gamma, iters, forced=forced)
+    res = cfse(s_grid, w_grid, gamma, iters, forced=forced, wfix_from=wfix_from)
     r0 = off + d
     patch = res.g.real[r0:r0 + b, r0:r0 + b].copy()
     return patch, res
 
 
 def conceal(images: np.ndarray, mask: np.ndarray, blocks: np.ndarray, classes,
-            forced=None, threads: int | None = None, keep_results: bool = False):
+            forced=None, threads: int | None = None, keep_results: bool = False,
+            wfix_from: int | None = None):
     """Conceal every block of ``blocks`` (rows: image, x, y, class index).
 
     images: [N, H, W] (u8 or float); mask: [N, H, W] u8 (1 = lost).
     classes: list of dicts with keys block, border, fft, rho, gamma, iters.
     forced: optional list (per block) of forced selection sequences.
+    wfix_from: reduced-precision residual storage (``oracle.cfse``).
     Returns (patches: list of b x b arrays, results or None).
     """
     images = np.asarray(images)
@@ -113,7 +117,7 @@ def conceal(images: np.ndarray, mask: np.ndarray, blocks: np.ndarray, classes,
     def one(i):
         im, x, y, c = (int(v) for v in blocks[i])
         f = None if forced is None else forced[i]
-        return conceal_block(images[im], mask[im], x, y, classes[c], forced=f)
+        return conceal_block(images[im], mask[im], x, y, classes[c], forced=f, wfix_from=wfix_from)
 
     if len(blocks) == 0:
         return [], ([] if keep_results else None)
