@@ -502,6 +502,31 @@ def ordered_leg(P, vid, mask, blocks, plain_patches, stream, dev):
             "psnr_db": ps(pt), "independent_psnr_db": ps(plain_patches)}
 
 
+def fixed_w_leg(P, vid, mask, blocks, plain_patches, plain_ms, args, stream, dev, peak_gbs):
+    """The headline batch with reduced-precision residual storage
+    (FSE_FLAG_FIXED_W: 16-bit fixed-point W after FSE_FIXED_W_FROM FP32
+    updates): blocks/s, speed-up over the FP32 kernel, PSNR of both, largest
+    pixel difference, and the shared-memory roofline with the mode's own
+    algorithmic bytes (8 B per bin for the FP32 updates, 4 B after)."""
+    import torch
+    from paper_2204_14193_gb300 import train_init
+    n = len(blocks)
+    truth = train_init.truth_patches(vid, blocks)
+    ps = lambda p: train_init.psnr(p.view(n, 16, 16), truth)  # noqa: E731
+    eng = P.Engine([CLS], fixed_w=True)
+    pf = torch.empty_like(plain_patches)
+    ms = timed_runs(eng, vid, mask, blocks, pf, max(3, min(args.steps, 10)), max(args.warmup, 2), stream, dev)
+    eng.close()
+    F, I, K = CLS["fft"], CLS["iters"], P.FSE_FIXED_W_FROM
+    k32 = min(K, I - 1)
+    bytes_block = 8.0 * k32 * F * F + 4.0 * (I - 1 - k32) * F * F + 96.0 * F * F
+    achieved = n * bytes_block / (ms / 1e3) / 1e9
+    return {"value": n / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms, "fixed_from": K,
+            "speedup_vs_fp32_w": plain_ms / ms, "psnr_db": ps(pf), "fp32_w_psnr_db": ps(plain_patches),
+            "max_abs_diff_vs_fp32_w": float((pf - plain_patches).abs().max().item()),
+            "smem_bytes_per_block": bytes_block, "smem_frac": achieved / peak_gbs}
+
+
 def run_reference(args):
     """The oracle as the reference arm (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -636,8 +661,9 @@ def main():
     if not args.no_learned and args.iters == 200:
         learned = learned_leg(P, vid, mask, blocks, patches, args, stream, dev)
         curve = learned_curve(P, vid, mask, blocks, stream, dev)
-    sweep = uneven = video = ordered = small = None
+    sweep = uneven = video = ordered = small = fixed = None
     if not args.no_extra and args.iters == 200:
+        fixed = fixed_w_leg(P, vid, mask, blocks, patches, ms, args, stream, dev, smem_peak)
         ordered = ordered_leg(P, vid, mask, blocks, patches, stream, dev)
         sweep = iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, smem_peak)
         uneven = uneven_batch(P, args, stream, dev, with_oracle=rank == 0 and not args.no_cpu_baseline,
@@ -689,7 +715,7 @@ def main():
                 "clocks": clocks, "gpu_launches": args.steps, "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cpu, "learned_init": learned, "learned_vs_plain": curve,
                 "iteration_sweep": sweep, "uneven_batch": uneven, "video_volumes": video, "ordered": ordered,
-                "small_configs": small}
+                "small_configs": small, "fixed_w": fixed}
         print(json.dumps(line))
     eng.close()
     if world > 1:

@@ -75,6 +75,21 @@ typedef enum {
  * as FP32).  Without it the output is the unclamped model Re{g} (Algorithm 1
  * produces real values; the paper does not round). */
 #define FSE_FLAG_CLAMP_U8 4u
+/* Reduced-precision residual storage (the Conclusion's remark that the method
+ * suits fixed-point arithmetic).  After the first FSE_FIXED_W_FROM residual
+ * updates of a block, the spectrum W that every update re-reads (Eq. (18))
+ * is held as 16-bit fixed-point codes q = round(W / W[0,0] * 32767) (round
+ * to nearest, ties to even, decided in FP32; |W| <= W[0,0] for a
+ * non-negative weight), half the shared-memory bytes per update; the
+ * residual R_w, c-hat and the model stay FP32.  The first updates carry the
+ * large coefficients and keep FP32 W: codes from the first update move the
+ * concealed samples by more than 1e-2, from the switch on they stay within
+ * 1e-2 of Algorithm 1 along the same selections.  Image classes of fft 64
+ * only, not with FSE_FLAG_ORDERED (FSE_ERR_UNSUPPORTED at fse_create);
+ * FSE_FLAG_TRACE records the selections but not the top-two gap
+ * (fse_get_trace_gap returns FSE_ERR_UNSUPPORTED). */
+#define FSE_FLAG_FIXED_W 8u
+#define FSE_FIXED_W_FROM 20   /* FP32 updates before the switch */
 
 /*
  * One block-size class.

@@ -19,8 +19,8 @@ from . import _build
 __all__ = ["fse_class", "fse_config", "fse_block", "FseError", "fse_create", "fse_extrapolate_batch",
            "fse_extrapolate_batch_host", "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_last_error", "fse_destroy", "Engine",
            "fse_measure_smem_bandwidth",
-           "library_path", "FSE_DTYPE_U8", "FSE_DTYPE_F32", "FSE_FLAG_TRACE", "FSE_INIT_ZERO",
-           "FSE_INIT_LEARNED"]
+           "library_path", "FSE_DTYPE_U8", "FSE_DTYPE_F32", "FSE_FLAG_TRACE", "FSE_FLAG_FIXED_W",
+           "FSE_FIXED_W_FROM", "FSE_INIT_ZERO", "FSE_INIT_LEARNED"]
 
 FSE_MAX_CLASSES = 4
 FSE_DTYPE_U8, FSE_DTYPE_F32 = 0, 1
@@ -28,6 +28,8 @@ FSE_INIT_ZERO, FSE_INIT_LEARNED = 0, 1
 FSE_FLAG_TRACE = 1
 FSE_FLAG_ORDERED = 2
 FSE_FLAG_CLAMP_U8 = 4
+FSE_FLAG_FIXED_W = 8
+FSE_FIXED_W_FROM = 20     # FP32 residual updates before the switch to 16-bit W
 STATUS = {0: "FSE_OK", 1: "FSE_ERR_INVALID_ARG", 2: "FSE_ERR_UNSUPPORTED", 3: "FSE_ERR_CUDA",
           4: "FSE_ERR_OOM", 5: "FSE_ERR_TIMEOUT", 6: "FSE_ERR_NOT_TRAINED"}
 
@@ -382,7 +384,7 @@ def he_init(seed: int) -> np.ndarray:
 # --------------------------------------------------------- convenience API
 def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero",
                 init_iters: int = 0, ordered: bool = False, reuse_weight: float = 0.5,
-                clamp_u8: bool = False) -> fse_config:
+                clamp_u8: bool = False, fixed_w: bool = False) -> fse_config:
     cfg = fse_config()
     cfg.n_classes = len(classes)
     for i, c in enumerate(classes):
@@ -392,7 +394,7 @@ def make_config(classes, device: int = 0, trace: bool = False, init: str = "zero
     cfg.init_iters = int(init_iters)
     cfg.device = device
     cfg.flags = ((FSE_FLAG_TRACE if trace else 0) | (FSE_FLAG_ORDERED if ordered else 0)
-                 | (FSE_FLAG_CLAMP_U8 if clamp_u8 else 0))
+                 | (FSE_FLAG_CLAMP_U8 if clamp_u8 else 0) | (FSE_FLAG_FIXED_W if fixed_w else 0))
     cfg.reuse_weight = float(reuse_weight)
     return cfg
 
@@ -401,13 +403,16 @@ class Engine:
     """A handle plus torch-tensor marshalling.
 
     classes: list of dicts with keys block, border, fft, rho, gamma, iters.
+    fixed_w: reduced-precision residual storage (FSE_FLAG_FIXED_W: 16-bit
+    fixed-point W after the first FSE_FIXED_W_FROM updates; fft 64 classes).
     """
 
     def __init__(self, classes, device: int = 0, trace: bool = False, init: str = "zero", init_iters: int = 0,
-                 weights=None, ordered: bool = False, reuse_weight: float = 0.5, clamp_u8: bool = False):
+                 weights=None, ordered: bool = False, reuse_weight: float = 0.5, clamp_u8: bool = False,
+                 fixed_w: bool = False):
         self.classes = [dict(c) for c in classes]
         self.h = fse_create(make_config(classes, device, trace, init, init_iters, ordered, reuse_weight,
-                                        clamp_u8))
+                                        clamp_u8, fixed_w))
         self.last_n = 0
         if weights is not None:
             fse_load_init_weights(self.h, weights)

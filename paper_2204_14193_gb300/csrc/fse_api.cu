@@ -84,7 +84,7 @@ struct fse_handle {
     int device = 0;
     int sm_count = 0;
     int cc = 0;                    // compute capability, major * 10 + minor
-    int max_ctas[4][2] = {};       // CTAs per SM of each kernel set (fse_device.cuh) x {128, 256} threads
+    int max_ctas[fse::kNumSets][2] = {};   // CTAs per SM of each kernel set (fse_device.cuh) x {128, 256} threads
     size_t smem_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     float *d_wtab[FSE_MAX_CLASSES] = {};
@@ -222,8 +222,17 @@ fse_status validate_config(const fse_config *cfg) {
         if (cfg->init_iters < 0 || cfg->init_iters > 4096)
             return fail(nullptr, FSE_ERR_INVALID_ARG, "init_iters %d not in [0, 4096]", cfg->init_iters);
     }
-    if (cfg->flags & ~(FSE_FLAG_TRACE | FSE_FLAG_ORDERED | FSE_FLAG_CLAMP_U8))
+    if (cfg->flags & ~(FSE_FLAG_TRACE | FSE_FLAG_ORDERED | FSE_FLAG_CLAMP_U8 | FSE_FLAG_FIXED_W))
         return fail(nullptr, FSE_ERR_INVALID_ARG, "unknown flag bits 0x%x", cfg->flags);
+    if (cfg->flags & FSE_FLAG_FIXED_W) {
+        // the 16-bit spectrum lives in the FFT-64 chunk layout
+        for (int c = 0; c < cfg->n_classes; ++c)
+            if (cfg->cls[c].fft != 64 || cfg->cls[c].frames > 1)
+                return fail(nullptr, FSE_ERR_UNSUPPORTED,
+                            "reduced-precision residual storage: image classes of fft 64 only");
+        if (cfg->flags & FSE_FLAG_ORDERED)
+            return fail(nullptr, FSE_ERR_UNSUPPORTED, "reduced-precision residual storage with ordered concealment");
+    }
     if (cfg->flags & FSE_FLAG_ORDERED) {
         // fft 16 is excluded: its blocks share warps, and a lane waiting for an
         // earlier block of its own warp would stall that warp's synchronisation
@@ -352,7 +361,8 @@ fse_status validate_and_plan(fse_handle *h, const void *images, int dtype, int n
         const fse_class &k = cfg.cls[pl.seg_cls[sg]];
         all_f64 = all_f64 && k.fft == 64 && k.frames <= 1;
     }
-    pl.ks = fse::kernel_set_for(h->ext, all_f64, (cfg.flags & FSE_FLAG_TRACE) != 0);
+    pl.ks = fse::kernel_set_for(h->ext, all_f64, (cfg.flags & FSE_FLAG_TRACE) != 0,
+                                (cfg.flags & FSE_FLAG_FIXED_W) != 0);
     const long long dev_key[5] = {pl.ks, h->sm_count, h->cc, (long long)h->smem_bytes,
                                   (long long)(cfg.flags & FSE_FLAG_ORDERED)};
     pl.tune_key = fnv1a(dev_key, sizeof dev_key, tkey);
@@ -406,7 +416,7 @@ EncodeTiledFn encode_tiled() {
 void setup_tma(const fse_handle *h, DevParams &P, int ks, int dtype, const void *images, const uint8_t *mask,
                int n_images, int height, int width, size_t pitch) {
     P.tma = 0;
-    if (ks != fse::kSetF64 || dtype != FSE_DTYPE_U8) return;
+    if ((ks != fse::kSetF64 && ks != fse::kSetFixW) || dtype != FSE_DTYPE_U8) return;
     if ((reinterpret_cast<uintptr_t>(images) & 15) || (reinterpret_cast<uintptr_t>(mask) & 15) || (pitch & 15) ||
         (width & 15) || (long long)n_images * height >= (1LL << 31))
         return;
@@ -837,6 +847,7 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     P.err = h->d_err;
     P.wait_ns = h->wait_ns;
     P.clamp_u8 = (h->cfg.flags & FSE_FLAG_CLAMP_U8) ? 1 : 0;
+    P.fix_from = FSE_FIXED_W_FROM;   // read by the reduced-precision kernel set only
     P.ordered = ordered ? 1 : 0;
     if (ordered) {
         std::vector<int> nb_start, nb_list;
@@ -971,6 +982,7 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
     P.err = h->d_err;
     P.wait_ns = h->wait_ns;
     P.clamp_u8 = (h->cfg.flags & FSE_FLAG_CLAMP_U8) ? 1 : 0;
+    P.fix_from = FSE_FIXED_W_FROM;   // read by the reduced-precision kernel set only
     set_classes(h, P, false);
     const size_t img_frame = (size_t)height * pitch, mask_frame = (size_t)height * width;
     int copied = 0;
@@ -1103,14 +1115,17 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     h->smem_bytes = smem;
     h->ext = (cfg->flags & FSE_FLAG_ORDERED) != 0;
     for (int c = 0; c < cfg->n_classes; ++c) h->ext = h->ext || cfg->cls[c].frames > 1;
-    // the kernel sets this handle's batches can run: the traced set, the
-    // extended set, or the image set and (with an FFT-64 class) the FFT-64 set
+    // the kernel sets this handle's batches can run: the reduced-precision
+    // set, the traced set, the extended set, or the image set and (with an
+    // FFT-64 class) the FFT-64 set
     bool any64 = false;
     for (int c = 0; c < cfg->n_classes; ++c) any64 = any64 || cfg->cls[c].fft == 64;
     const bool traced = (cfg->flags & FSE_FLAG_TRACE) != 0;
-    for (int ks : {fse::kSetImage, fse::kSetExt, fse::kSetF64, fse::kSetTrace}) {
-        if (traced != (ks == fse::kSetTrace)) continue;
-        if (!traced && ((ks == fse::kSetExt) != h->ext || (ks == fse::kSetF64 && !any64))) continue;
+    const bool fixw = (cfg->flags & FSE_FLAG_FIXED_W) != 0;
+    for (int ks : {fse::kSetImage, fse::kSetExt, fse::kSetF64, fse::kSetTrace, fse::kSetFixW}) {
+        if (fixw != (ks == fse::kSetFixW)) continue;
+        if (!fixw && traced != (ks == fse::kSetTrace)) continue;
+        if (!fixw && !traced && ((ks == fse::kSetExt) != h->ext || (ks == fse::kSetF64 && !any64))) continue;
         for (int t = 0; t < 2; ++t) {
             int occ = 0;
             CREATE_CUDA(fse::batch_kernel_prepare(ks, t ? 256 : 128, smem, &occ));
@@ -1272,6 +1287,8 @@ fse_status fse_get_trace(fse_handle *h, int32_t *sel, float *energy, float *coef
 fse_status fse_get_trace_gap(fse_handle *h, float *gap2, size_t cap) {
     if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
     if (!(h->cfg.flags & FSE_FLAG_TRACE)) return fail(h, FSE_ERR_INVALID_ARG, "handle was created without FSE_FLAG_TRACE");
+    if (h->cfg.flags & FSE_FLAG_FIXED_W)
+        return fail(h, FSE_ERR_UNSUPPORTED, "the top-two gap is not recorded with FSE_FLAG_FIXED_W");
     DeviceGuard guard(h->device);
     const size_t n = (size_t)h->last_n_blocks * h->tr_stride;
     if (n == 0) return FSE_OK;

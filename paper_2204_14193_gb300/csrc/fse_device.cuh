@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 namespace fse {
 
@@ -87,6 +88,10 @@ struct DevParams {
     int *err;                         // device status word: kErr* bits (nullptr: not reported)
     unsigned long long wait_ns;       // limit of every bounded device wait
     int clamp_u8;                     // outputs clamped to [0, 255] and rounded half to even
+    // reduced-precision residual storage (kSetFixW): the updates of
+    // iterations fix_from, fix_from + 1, ... (0-based) read W as 16-bit
+    // fixed-point codes of W / W[0,0] (scale 32767) instead of FP32
+    int fix_from;
     // F = 64 windows of 8-bit images fetched as tiles by the tensor-memory
     // accelerator: 2-D maps over [n_images * H rows, W columns] of the images
     // and the mask, box tma_bw columns x tma_bh rows (tma = 0: plain loads)
@@ -137,6 +142,38 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---- 16-bit fixed-point spectrum (reduced-precision residual storage) ----
+// A value x of W is held as the code q = rint(x * 32767 / W[0,0]) in
+// [-32767, 32767] (|W| <= W[0,0] for a non-negative weight), stored biased as
+// the 16-bit integer q + 32768.  Decoding needs no conversion instruction:
+// the 16 bits placed under the exponent of 2^23 form the float 2^23 + q +
+// 32768, and subtracting 2^23 + 32768 (exact: both lie in [2^23, 2^24))
+// leaves q.  The update then multiplies q by c W[0,0] / 32767.
+constexpr uint32_t kFixMagic = 0x4B000000u;        // bits of 2^23
+constexpr float kFixBias = 8421376.f;              // 2^23 + 32768
+
+__device__ __forceinline__ uint32_t fix_code16(float x, float qs) {
+    const float q = fminf(fmaxf(rintf(x * qs), -32767.f), 32767.f);
+    return (uint32_t)((int)q + 32768);
+}
+
+// codes of (a, b) as one word: a in the low half, b in the high half
+__device__ __forceinline__ uint32_t fix_pack(float a, float b, float qs) {
+    return fix_code16(a, qs) | (fix_code16(b, qs) << 16);
+}
+
+// the codes of one word as an f32x2 pair (low half, high half)
+__device__ __forceinline__ uint64_t fix_unpack(uint32_t w, uint64_t nbias2) {
+    const uint32_t lo = __byte_perm(w, kFixMagic, 0x7610), hi = __byte_perm(w, kFixMagic, 0x7632);
+    return add2((uint64_t)lo | ((uint64_t)hi << 32), nbias2);
+}
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -234,7 +271,8 @@ __host__ __device__ constexpr int cta_region_bytes(int F) { return F == 64 ? 16 
 constexpr int kMaxWarps = 8;
 
 // kernel sets of fse_batch_kernel (see there)
-constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2, kSetTrace = 3;
+constexpr int kSetImage = 0, kSetExt = 1, kSetF64 = 2, kSetTrace = 3, kSetFixW = 4;
+constexpr int kNumSets = 5;
 
 struct RedShared {
     uint4 win[2][kMaxWarps];   // per-warp argmax candidates, double-buffered by iteration parity
@@ -316,6 +354,40 @@ __device__ __forceinline__ void gsync(const Grp &gr) {
 // Maximum of a non-negative float over the group.  A maximum does not depend
 // on the order in which it is taken, so the result is the same for every
 // thread-to-bin mapping the autotuner may choose.
+// The switch to reduced-precision residual storage: every 16-byte FP32 chunk
+// e of the block's W (Geo::REGION) becomes the 8-byte chunk e of 16-bit codes
+// {Re W, Re W'}, {Im W, Im W'} (same dual-chunk order), in place.  Rounds of
+// RND chunks: a round reads its FP32 chunks into registers, waits for the
+// group, then writes its code chunks.  The codes of round r land in bytes
+// [8 lo, 8 hi) of FP32 chunks lo .. hi - 1, below 16 hi, so they overwrite only
+// chunks that this or an earlier round has read, and the next round's reads
+// (from byte 16 hi on) are untouched: one group barrier per round.
+template <int F, int PAIRS, int NT>
+__device__ __forceinline__ void compact_w(unsigned char *region, float qs, const Grp &gr) {
+    using G = Geo<F, PAIRS>;
+    constexpr int TB = G::TB, NCH = G::WROWS * F, CPT = 2, RND = TB * CPT;
+    const float4 *src = reinterpret_cast<const float4 *>(region);
+    uint2 *dst = reinterpret_cast<uint2 *>(region);
+    for (int base = 0; base < NCH; base += RND) {
+        uint2 cv[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int e = base + j * TB + gr.lt;
+            if (e < NCH) {
+                const float4 f = src[e];
+                cv[j] = make_uint2(fix_pack(f.x, f.y, qs), fix_pack(f.z, f.w, qs));
+            }
+        }
+        gsync<F, PAIRS, NT>(gr);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int e = base + j * TB + gr.lt;
+            if (e < NCH) dst[e] = cv[j];
+        }
+    }
+    gsync<F, PAIRS, NT>(gr);
+}
+
 template <int F, int PAIRS, int NT, int FT = 1>
 __device__ __forceinline__ float group_max(float v, const Grp &gr, RedShared *rs) {
     using G = Geo<F, PAIRS, FT>;
@@ -600,11 +672,16 @@ __device__ __forceinline__ Pick group_argmax(const uint64_t *Rre, const uint64_t
 // NP: B samples per thread (compile time; the caller picks the smallest
 // variant that covers b*b).  EXT: built with ordered concealment.  GAP: the
 // traced kernel set (selection trace with the top-two gap; other sets write
-// no trace).  TMA: the FFT-64 set (windows of 8-bit images by TMA).
-template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false, bool TMA = false>
+// no trace).  TMA: the FFT-64 sets (windows of 8-bit images by TMA).  FIXW:
+// reduced-precision residual storage from iteration P.fix_from on (its set
+// also writes the selection trace, without the gap).
+template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false, bool TMA = false,
+          bool FIXW = false>
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh, uint32_t &tph) {
     using G = Geo<F, PAIRS>;
+    static_assert(!FIXW || G::RUNS, "the fixed-point spectrum uses the F = 64 chunk rows");
+    constexpr bool TRW = GAP || FIXW;   // trace writes compiled in
     constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
     Grp gr;
     gr.g = threadIdx.x / TB;
@@ -821,74 +898,179 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     const bool gap = GAP && P.tr_second != nullptr;
     if (iters > 0) pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, 0, gap);
 
-    const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
-    for (int nu = 1; nu <= iters; ++nu) {
-        // ---- S6/S7: coefficient and model ----
-        const float cr = pick.rr * cg, ci = pick.ri * cg;
-        const int u = (int)(pick.idx / F), v = (int)(pick.idx % F);
-        if (GAP && P.tr_sel != nullptr && lt == 0) {   // traced launches (their own kernel set)
-            const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
-            P.tr_sel[o] = (int)pick.idx;
-            P.tr_energy[o] = __uint_as_float(pick.ebits);
-            P.tr_coef[o] = make_float2(cr, ci);
-            if (P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
-        }
-        // model update of this selection, evaluated on B: g += c phi_(u,v)
-        // (independent of the residual update and of the next reduction)
-        auto model = [&]() {
-#pragma unroll
-            for (int t = 0; t < NP; ++t) {
-                const int ph = (u * pm_[t] + v * pn_[t]) & (F - 1);
-                const float2 tw = s_tw[ph * (64 / F)];
-                acc[t] = fmaf(cr, tw.x, fmaf(-ci, tw.y, acc[t]));
+    if constexpr (!FIXW) {
+        const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
+        for (int nu = 1; nu <= iters; ++nu) {
+            // ---- S6/S7: coefficient and model ----
+            const float cr = pick.rr * cg, ci = pick.ri * cg;
+            const int u = (int)(pick.idx / F), v = (int)(pick.idx % F);
+            if (GAP && P.tr_sel != nullptr && lt == 0) {   // traced launches (their own kernel set)
+                const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
+                P.tr_sel[o] = (int)pick.idx;
+                P.tr_energy[o] = __uint_as_float(pick.ebits);
+                P.tr_coef[o] = make_float2(cr, ci);
+                if (P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
             }
-        };
-        if (nu == iters) {
+            // model update of this selection, evaluated on B: g += c phi_(u,v)
+            // (independent of the residual update and of the next reduction)
+            auto model = [&]() {
+    #pragma unroll
+                for (int t = 0; t < NP; ++t) {
+                    const int ph = (u * pm_[t] + v * pn_[t]) & (F - 1);
+                    const float2 tw = s_tw[ph * (64 / F)];
+                    acc[t] = fmaf(cr, tw.x, fmaf(-ci, tw.y, acc[t]));
+                }
+            };
+            if (nu == iters) {
+                model();
+                break;
+            }
+            // ---- S8: R_w[k,l] -= c W[k-u, l-v] fused with |R_w|^2 and max ----
+            const uint64_t ncr = pk(-cr, -cr), pci = pk(ci, ci), nci = pk(-ci, -ci);
+            // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
+            // at pair iw.  Pairs before the wrap address from A, the others from
+            // A - F*F, so each load needs one select and an immediate offset.
+            // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
+            // contiguous in W (rows F.. repeat rows 0..6): one base per run.
+            const int qcol = (c0 - v) & (F - 1);
+            const int rb = (r0 - u) & (F - 1);
+            const int iw = (F - rb + RSTEP - 1) / RSTEP;
+            const ulonglong2 *A = Wq + rb * F + qcol;
+            const ulonglong2 *A2 = A - F * F;
+            const ulonglong2 *Ar[G::RUNS ? PAIRS / 8 : 1];
+    #pragma unroll
+            for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
+                Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+            tmax = 0.f;
+    #pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                float ev[8];
+    #pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    const int i = 4 * j + ii;
+                    // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
+                    const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                                                 : (i < iw ? A : A2)[i * RSTEP * F];
+                    const uint64_t wre = w.x, wim = w.y;
+                    uint64_t a = fma2(ncr, wre, Rre[i]);
+                    Rre[i] = fma2(pci, wim, a);
+                    uint64_t bb = fma2(ncr, wim, Rim[i]);
+                    Rim[i] = fma2(nci, wre, bb);
+                    const uint64_t e = energy2(Rre[i], Rim[i]);
+                    ev[2 * ii] = lo_of(e);
+                    ev[2 * ii + 1] = hi_of(e);
+                }
+                const float a = max3f(ev[0], ev[1], ev[2]);
+                const float bq = max3f(ev[3], ev[4], ev[5]);
+                quartet_max(j, max3f(a, bq, fmaxf(ev[6], ev[7])), tmax, jb);
+            }
             model();
-            break;
+            // ---- S5: next selection ----
+            pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, nu & 1, gap);
         }
-        // ---- S8: R_w[k,l] -= c W[k-u, l-v] fused with |R_w|^2 and max ----
-        const uint64_t ncr = pk(-cr, -cr), pci = pk(ci, ci), nci = pk(-ci, -ci);
-        // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
-        // at pair iw.  Pairs before the wrap address from A, the others from
-        // A - F*F, so each load needs one select and an immediate offset.
-        // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
-        // contiguous in W (rows F.. repeat rows 0..6): one base per run.
-        const int qcol = (c0 - v) & (F - 1);
-        const int rb = (r0 - u) & (F - 1);
-        const int iw = (F - rb + RSTEP - 1) / RSTEP;
-        const ulonglong2 *A = Wq + rb * F + qcol;
-        const ulonglong2 *A2 = A - F * F;
-        const ulonglong2 *Ar[G::RUNS ? PAIRS / 8 : 1];
-#pragma unroll
-        for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
-            Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
-        tmax = 0.f;
-#pragma unroll
-        for (int j = 0; j < NQ; ++j) {
-            float ev[8];
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii) {
-                const int i = 4 * j + ii;
-                // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
-                                             : (i < iw ? A : A2)[i * RSTEP * F];
-                const uint64_t wre = w.x, wim = w.y;
-                uint64_t a = fma2(ncr, wre, Rre[i]);
-                Rre[i] = fma2(pci, wim, a);
-                uint64_t bb = fma2(ncr, wim, Rim[i]);
-                Rim[i] = fma2(nci, wre, bb);
-                const uint64_t e = energy2(Rre[i], Rim[i]);
-                ev[2 * ii] = lo_of(e);
-                ev[2 * ii + 1] = hi_of(e);
+    } else {
+        // One iteration: coefficient and model of pick nu, then (unless it is the
+        // last) the residual update and the next pick.  FX: the update reads the
+        // 16-bit codes of W (after the switch) instead of FP32 W.  Returns true
+        // after the last iteration.
+        const float dq = W00 * (1.f / 32767.f);   // value of one code step (FX)
+        auto step = [&](int nu, auto fx) -> bool {
+            constexpr bool FX = decltype(fx)::value;
+            // ---- S6/S7: coefficient and model ----
+            const float cr = pick.rr * cg, ci = pick.ri * cg;
+            const int u = (int)(pick.idx / F), v = (int)(pick.idx % F);
+            if (TRW && P.tr_sel != nullptr && lt == 0) {   // traced launches (their own kernel sets)
+                const size_t o = (size_t)blk.orig * P.tr_stride + (nu - 1);
+                P.tr_sel[o] = (int)pick.idx;
+                P.tr_energy[o] = __uint_as_float(pick.ebits);
+                P.tr_coef[o] = make_float2(cr, ci);
+                if (GAP && P.tr_second != nullptr) P.tr_second[o] = __uint_as_float(pick.sbits);
             }
-            const float a = max3f(ev[0], ev[1], ev[2]);
-            const float bq = max3f(ev[3], ev[4], ev[5]);
-            quartet_max(j, max3f(a, bq, fmaxf(ev[6], ev[7])), tmax, jb);
+            // model update of this selection, evaluated on B: g += c phi_(u,v)
+            // (independent of the residual update and of the next reduction)
+            auto model = [&]() {
+    #pragma unroll
+                for (int t = 0; t < NP; ++t) {
+                    const int ph = (u * pm_[t] + v * pn_[t]) & (F - 1);
+                    const float2 tw = s_tw[ph * (64 / F)];
+                    acc[t] = fmaf(cr, tw.x, fmaf(-ci, tw.y, acc[t]));
+                }
+            };
+            if (nu == iters) {
+                model();
+                return true;
+            }
+            // ---- S8: R_w[k,l] -= c W[k-u, l-v] fused with |R_w|^2 and max ----
+            // (FX: c scaled to code units, W read as codes)
+            const float sr = FX ? cr * dq : cr, si = FX ? ci * dq : ci;
+            const uint64_t ncr = pk(-sr, -sr), pci = pk(si, si), nci = pk(-si, -si);
+            const uint64_t nbias2 = pk(-kFixBias, -kFixBias);
+            // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
+            // at pair iw.  Pairs before the wrap address from A, the others from
+            // A - F*F, so each load needs one select and an immediate offset.
+            // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
+            // contiguous in W (rows F.. repeat rows 0..6): one base per run.
+            using Chunk = typename std::conditional<FX, uint2, ulonglong2>::type;
+            const Chunk *Wq = reinterpret_cast<const Chunk *>(region);
+            const int qcol = (c0 - v) & (F - 1);
+            const int rb = (r0 - u) & (F - 1);
+            const int iw = (F - rb + RSTEP - 1) / RSTEP;
+            const Chunk *A = Wq + rb * F + qcol;
+            const Chunk *A2 = A - F * F;
+            const Chunk *Ar[G::RUNS ? PAIRS / 8 : 1];
+    #pragma unroll
+            for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
+                Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+            tmax = 0.f;
+    #pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                float ev[8];
+    #pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    const int i = 4 * j + ii;
+                    // one load: (Re W, Re W') and (Im W, Im W') as two f32x2
+                    // operands (16 bytes of FP32, or 8 bytes of codes)
+                    const Chunk w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                                            : (i < iw ? A : A2)[i * RSTEP * F];
+                    uint64_t wre, wim;
+                    if constexpr (FX) {
+                        wre = fix_unpack(w.x, nbias2);
+                        wim = fix_unpack(w.y, nbias2);
+                    } else {
+                        wre = w.x;
+                        wim = w.y;
+                    }
+                    uint64_t a = fma2(ncr, wre, Rre[i]);
+                    Rre[i] = fma2(pci, wim, a);
+                    uint64_t bb = fma2(ncr, wim, Rim[i]);
+                    Rim[i] = fma2(nci, wre, bb);
+                    const uint64_t e = energy2(Rre[i], Rim[i]);
+                    ev[2 * ii] = lo_of(e);
+                    ev[2 * ii + 1] = hi_of(e);
+                }
+                const float a = max3f(ev[0], ev[1], ev[2]);
+                const float bq = max3f(ev[3], ev[4], ev[5]);
+                quartet_max(j, max3f(a, bq, fmaxf(ev[6], ev[7])), tmax, jb);
+            }
+            model();
+            // ---- S5: next selection ----
+            pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, nu & 1, gap);
+            return false;
+        };
+        // updates before the switch: all of them unless FIXW
+        int kfix = iters;
+        if constexpr (FIXW) kfix = min(iters, max(P.fix_from, 0));
+        for (int nu = 1; nu <= kfix; ++nu)
+            if (step(nu, std::false_type{})) break;
+        if constexpr (FIXW) {
+            if (kfix < iters) {
+                // W's FP32 chunks -> codes; the codes are decided in FP32 with the
+                // scale 32767 / W[0,0]
+                compact_w<F, PAIRS, NT>(region, 32767.f * W0bar, gr);
+                for (int nu = kfix + 1; nu <= iters; ++nu)
+                    if (step(nu, std::true_type{})) break;
+            }
         }
-        model();
-        // ---- S5: next selection ----
-        pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, nu & 1, gap);
     }
 
     // ---- S10: write Re{g} on B ----
@@ -1210,7 +1392,8 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     }
 }
 
-template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false, bool GAP = false, bool TMA = false>
+template <int F, int PAIRS, int NT, int FT = 1, bool EXT = false, bool GAP = false, bool TMA = false,
+          bool FIXW = false>
 __device__ __forceinline__ void process_class(const DevParams &P, const DevClass &C, int first, int count,
                                               unsigned char *smem, const float2 *s_tw, RedShared *rsh,
                                               uint32_t &tph) {
@@ -1218,8 +1401,9 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
     if constexpr (FT == 1) {
         constexpr int NPS = PAIRS >= 16 ? 2 : 1;      // covers b <= F/4
         constexpr int NPL = PAIRS / 2;                // covers b <= F/2
-        if (C.b * C.b <= TB * NPS) process<F, PAIRS, NT, NPS, EXT, GAP, TMA>(P, C, first, count, smem, s_tw, rsh, tph);
-        else process<F, PAIRS, NT, NPL, EXT, GAP, TMA>(P, C, first, count, smem, s_tw, rsh, tph);
+        if (C.b * C.b <= TB * NPS)
+            process<F, PAIRS, NT, NPS, EXT, GAP, TMA, FIXW>(P, C, first, count, smem, s_tw, rsh, tph);
+        else process<F, PAIRS, NT, NPL, EXT, GAP, TMA, FIXW>(P, C, first, count, smem, s_tw, rsh, tph);
     } else {
         // a volume's block group is FT times larger: b <= F/2 needs
         // F^2/4 / TB = PAIRS / (2 FT) samples per thread (at least 1)
@@ -1236,6 +1420,9 @@ __device__ __forceinline__ void process_class(const DevParams &P, const DevClass
 //   kSetF64    image classes of FFT size 64 only
 //   kSetTrace  everything kSetExt runs, plus the trace's top-two gap (the
 //              largest energy besides each pick): traced batches only
+//   kSetFixW   image classes of FFT size 64 with reduced-precision residual
+//              storage (16-bit fixed-point W from iteration P.fix_from on;
+//              writes the selection trace when one is requested)
 // A batch runs the smallest set that covers its classes, so the code and
 // register allocation of the common cases are not burdened by the others.
 template <int NT, int KS>
@@ -1248,7 +1435,7 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
     __shared__ int s_item;
     __shared__ RedShared rsh;
     for (int i = threadIdx.x; i < 64; i += NT) s_tw[i] = P.tw[i];
-    if (KS == kSetF64 && threadIdx.x == 0 && P.tma) mbar_init(&rsh.mbar, 1);
+    if ((KS == kSetF64 || KS == kSetFixW) && threadIdx.x == 0 && P.tma) mbar_init(&rsh.mbar, 1);
     uint32_t tph = 0;   // phase of rsh.mbar the next window waits for
     __syncthreads();
     for (;;) {
@@ -1269,6 +1456,8 @@ __global__ void __launch_bounds__(NT, 3) fse_batch_kernel(const __grid_constant_
             }
         } else if constexpr (KS == kSetF64) {
             process_class<64, PAIRS, NT, 1, false, false, true>(P, C, first, count, smem, s_tw, &rsh, tph);
+        } else if constexpr (KS == kSetFixW) {
+            process_class<64, PAIRS, NT, 1, false, false, true, true>(P, C, first, count, smem, s_tw, &rsh, tph);
         } else {
             switch (C.F) {
                 case 64: process_class<64, PAIRS, NT, 1, EXT, GAP>(P, C, first, count, smem, s_tw, &rsh, tph); break;

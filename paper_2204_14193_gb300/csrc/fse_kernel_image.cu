@@ -23,14 +23,15 @@ cudaError_t batch_kernel_launch_image(int nt, int grid, size_t smem, cudaStream_
     return cudaGetLastError();
 }
 
-int kernel_set_for(bool ext, bool all_f64, bool trace) {
-    return trace ? kSetTrace : ext ? kSetExt : all_f64 ? kSetF64 : kSetImage;
+int kernel_set_for(bool ext, bool all_f64, bool trace, bool fixw) {
+    return fixw ? kSetFixW : trace ? kSetTrace : ext ? kSetExt : all_f64 ? kSetF64 : kSetImage;
 }
 
 cudaError_t batch_kernel_prepare(int ks, int nt, size_t smem, int *ctas_per_sm) {
     if (ks == kSetExt) return batch_kernel_prepare_ext(nt, smem, ctas_per_sm);
     if (ks == kSetTrace) return batch_kernel_prepare_trace(nt, smem, ctas_per_sm);
     if (ks == kSetF64) return batch_kernel_prepare_f64(nt, smem, ctas_per_sm);
+    if (ks == kSetFixW) return batch_kernel_prepare_fixw(nt, smem, ctas_per_sm);
     return batch_kernel_prepare_image(nt, smem, ctas_per_sm);
 }
 
@@ -38,6 +39,7 @@ cudaError_t batch_kernel_launch(int ks, int nt, int grid, size_t smem, cudaStrea
     if (ks == kSetExt) return batch_kernel_launch_ext(nt, grid, smem, s, P);
     if (ks == kSetTrace) return batch_kernel_launch_trace(nt, grid, smem, s, P);
     if (ks == kSetF64) return batch_kernel_launch_f64(nt, grid, smem, s, P);
+    if (ks == kSetFixW) return batch_kernel_launch_fixw(nt, grid, smem, s, P);
     return batch_kernel_launch_image(nt, grid, smem, s, P);
 }
 }  // namespace fse

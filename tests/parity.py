@@ -34,6 +34,15 @@ EPS_TIE = 1e-5      # near-tie band of the top-two energies (relative)
 ROUND_K = 4.0       # reported only: how far a delta-widened band would reach
 DELTA_MAX = 2e-4    # largest FP32 energy deviation accepted at any pick
 PIX_TOL = 1e-2      # absolute pixel tolerance, 0-255 scale
+# Reduced-precision residual storage (wfix_from): the kernel decides each
+# 16-bit code of W from its FP32 spectrum, the oracle from its FP64 one, so
+# about 0.6% of the codes differ by one step, and the energies of the two
+# quantised residuals drift apart by more than FP32 rounding does (measured
+# on the GB300: 1.0e-3 at worst over 51,200 picks).  DELTA_FIX bounds that
+# deviation; every pick is then an argmax of the oracle's residual up to
+# EPS_FIX = 2 DELTA_FIX (each energy is off by at most DELTA_FIX relative).
+DELTA_FIX = 3e-3
+EPS_FIX = 2 * DELTA_FIX
 
 
 def mirror(sel, F):
@@ -41,12 +50,17 @@ def mirror(sel, F):
     return ((-(sel // F)) % F) * F + ((-(sel % F)) % F)
 
 
-def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, est=None, iters=None):
+def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, est=None, iters=None,
+                wfix_from=None):
     """Compare one block.  Returns a dict of diagnostics; raises nothing.
     gpu_sel / gpu_energy: the kernel's selection trace and FP32 energies.
     est: warm start, the M x M area estimate (the model then starts from the
     residual s - est on the support and the output is est + Re{g} on B).
-    iters: iteration count in place of the class's."""
+    iters: iteration count in place of the class's.
+    wfix_from: reduced-precision residual storage from that iteration on;
+    every criterion then uses the oracle of that form, and exact_pix reports
+    the pixel difference to the exact oracle replayed along the GPU's
+    selections."""
     im, x, y, c = (int(v) for v in blk)
     k = cls[c]
     F, b, I = k["fft"], k["block"], k["iters"] if iters is None else iters
@@ -61,8 +75,8 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
         est_b = est[k["border"]:k["border"] + b, k["border"]:k["border"] + b]
     out = dict(ok=True, first_div=None, max_pix=0.0, worst_ratio=1.0, mirror=False,
                max_delta=0.0, widened=False, picks=0, wide_picks=0, wide_gap=0.0, wide_delta=0.0,
-               free_pix=0.0)
-    free = oracle.cfse(s_grid, w_grid, k["gamma"], I)
+               free_pix=0.0, exact_pix=0.0)
+    free = oracle.cfse(s_grid, w_grid, k["gamma"], I, wfix_from=wfix_from)
     r0 = off + k["border"]
     free_patch = free.g.real[r0:r0 + b, r0:r0 + b] + est_b
     out["free_pix"] = float(np.max(np.abs(free_patch - gpu_patch))) if b else 0.0
@@ -84,7 +98,11 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
             a = int(np.argmin(same)) if not same.all() else I
             bq = int(np.argmin(mir)) if not mir.all() else I
             out["first_div"] = max(a, bq)
-    guided = oracle.cfse(s_grid, w_grid, k["gamma"], I, forced=gsel.astype(np.int32))
+    guided = oracle.cfse(s_grid, w_grid, k["gamma"], I, forced=gsel.astype(np.int32), wfix_from=wfix_from)
+    if wfix_from is not None:
+        exact = oracle.cfse(s_grid, w_grid, k["gamma"], I, forced=gsel.astype(np.int32))
+        ex_patch = exact.g.real[r0:r0 + b, r0:r0 + b] + est_b
+        out["exact_pix"] = float(np.max(np.abs(ex_patch - gpu_patch))) if b else 0.0
     if I:
         ratio = guided.e_sel / np.maximum(guided.e_max, 1e-300)
         ratio[guided.e_max == 0] = 1.0
@@ -96,7 +114,8 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
         else:
             delta = np.zeros(I)
         out["max_delta"] = float(delta.max())
-        if np.any(1.0 - ratio > EPS_TIE) or out["max_delta"] > DELTA_MAX:
+        eps, dmax = (EPS_TIE, DELTA_MAX) if wfix_from is None else (EPS_FIX, DELTA_FIX)
+        if np.any(1.0 - ratio > eps) or out["max_delta"] > dmax:
             out["ok"] = False
         wide = 1.0 - ratio > EPS_TIE
         out["widened"] = bool(np.any(wide))
@@ -167,10 +186,11 @@ def check_block3(video, mask, blk, cls, gpu_patch, gpu_sel, gpu_energy):
     return out
 
 
-def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None, ests=None, iters=None):
+def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None, ests=None, iters=None,
+                wfix_from=None):
     """Check every block of a batch; patches is the flat patch array (caller
     order), sels / energies the [n, stride] trace or None, ests the per-block
-    warm-start estimates [n, >= M*M] or None."""
+    warm-start estimates [n, >= M*M] or None, wfix_from as check_block."""
     blocks = np.asarray(blocks).reshape(-1, 4)
     offs = np.zeros(len(blocks) + 1, np.int64)
     for i, bk in enumerate(blocks):
@@ -185,7 +205,7 @@ def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, th
                            None if sels is None else sels[i],
                            None if energies is None else energies[i],
                            None if ests is None else ests[i][:(b + 2 * cls[int(bk[3])]["border"]) ** 2],
-                           iters)
+                           iters, wfix_from)
 
     n = threads or len(os.sched_getaffinity(0))
     with ThreadPoolExecutor(max_workers=n) as ex:
@@ -210,7 +230,8 @@ def summarize(results):
                 wide_delta=max((r.get("wide_delta", 0.0) for r in results), default=0.0),
                 div_frac=n_div / max(len(results), 1),
                 div_first=min((r["first_div"] for r in div), default=None),
-                div_free_pix=max((r.get("free_pix", 0.0) for r in div), default=0.0))
+                div_free_pix=max((r.get("free_pix", 0.0) for r in div), default=0.0),
+                exact_pix=max((r.get("exact_pix", 0.0) for r in results), default=0.0))
 
 
 # Bounds per batch: picks outside the near-tie band (none: the check above
@@ -223,9 +244,10 @@ MAX_WIDE_FRAC = 0.0      # of all picks of a batch
 MAX_DIV_FRAC = 0.2       # of the blocks of a batch (with at least 20 blocks)
 
 
-def assert_strict_bounds(s, min_blocks=20):
+def assert_strict_bounds(s, min_blocks=20, max_wide=MAX_WIDE_FRAC):
     """The strict-band bounds on a summarize() result (batches of at least
-    min_blocks blocks for the divergence bound)."""
-    assert s["wide_frac"] <= MAX_WIDE_FRAC, s
+    min_blocks blocks for the divergence bound); max_wide: the fraction of
+    picks allowed outside EPS_TIE."""
+    assert s["wide_frac"] <= max_wide, s
     if s["n"] >= min_blocks:
         assert s["div_frac"] <= MAX_DIV_FRAC, s

@@ -90,3 +90,24 @@ def test_ordered_config_validation(kw, status):
     with pytest.raises(P.FseError) as ei:
         P.fse_create(P.make_config([cls] * n, **kw))
     assert ei.value.status == status
+
+
+@pytest.mark.parametrize("kw,status", [(dict(fft=32), 2), (dict(frames=3), 2), (dict(ordered=True), 2),
+                                       (dict(bits=0x10), 1)])
+def test_fixed_w_config_validation(kw, status):
+    """Reduced-precision residual storage: image classes of fft 64 only, not
+    with ordered concealment; unknown flag bits are rejected."""
+    cls = dict(block=16, border=16, fft=64, rho=0.8, gamma=0.5, iters=10)
+    if "fft" in kw:
+        cls = dict(block=8, border=12, fft=kw.pop("fft"), rho=0.8, gamma=0.5, iters=10)
+    if "frames" in kw:
+        cls = dict(block=8, border=12, fft=32, rho=0.8, gamma=0.5, iters=10, frames=kw.pop("frames"))
+    bits = kw.pop("bits", 0)
+    cfg = P.make_config([cls], fixed_w=True, **kw)
+    cfg.flags |= bits
+    with pytest.raises(P.FseError) as ei:
+        P.fse_create(cfg)
+    assert ei.value.status == status
+    hdr = open(HEADER).read()
+    assert re.search(r"#define FSE_FLAG_FIXED_W (\d+)u", hdr).group(1) == str(P.FSE_FLAG_FIXED_W)
+    assert re.search(r"#define FSE_FIXED_W_FROM (\d+)", hdr).group(1) == str(P.FSE_FIXED_W_FROM)
