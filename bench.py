@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the I sweep and the uneven-size batch")
     ap.add_argument("--init-iters", type=int, default=50)
     ap.add_argument("--init-weights", default=None, help="network parameters (.f32) for the learned leg")
+    ap.add_argument("--fixed-w", action="store_true",
+                    help="time the headline with reduced-precision residual storage (FSE_FLAG_FIXED_W)")
     return ap.parse_args()
 
 
@@ -210,6 +212,14 @@ def smem_bytes_per_block(F: int, I: int) -> float:
     the grid for the weighting, the two FFT passes (two steps each, loads and
     stores) and the split into R_w and W."""
     return 8.0 * I * F * F + 96.0 * F * F
+
+
+def fixed_w_bytes_per_block(F: int, I: int, K: int) -> float:
+    """smem_bytes_per_block with reduced-precision residual storage, counted
+    the same way (one W operand per bin and iteration): 8-byte FP32 operands
+    for the first K iterations, 4-byte codes for the other I - K."""
+    k32 = min(K, I)
+    return 8.0 * k32 * F * F + 4.0 * (I - k32) * F * F + 96.0 * F * F
 
 
 def timed_runs(eng, vid, mask, blocks, patches, steps, warmup, stream, dev):
@@ -507,7 +517,7 @@ def fixed_w_leg(P, vid, mask, blocks, plain_patches, plain_ms, args, stream, dev
     (FSE_FLAG_FIXED_W: 16-bit fixed-point W after FSE_FIXED_W_FROM FP32
     updates): blocks/s, speed-up over the FP32 kernel, PSNR of both, largest
     pixel difference, and the shared-memory roofline with the mode's own
-    algorithmic bytes (8 B per bin for the FP32 updates, 4 B after)."""
+    algorithmic bytes (8 B per bin for the FP32 iterations, 4 B after)."""
     import torch
     from paper_2204_14193_gb300 import train_init
     n = len(blocks)
@@ -518,8 +528,7 @@ def fixed_w_leg(P, vid, mask, blocks, plain_patches, plain_ms, args, stream, dev
     ms = timed_runs(eng, vid, mask, blocks, pf, max(3, min(args.steps, 10)), max(args.warmup, 2), stream, dev)
     eng.close()
     F, I, K = CLS["fft"], CLS["iters"], P.FSE_FIXED_W_FROM
-    k32 = min(K, I - 1)
-    bytes_block = 8.0 * k32 * F * F + 4.0 * (I - 1 - k32) * F * F + 96.0 * F * F
+    bytes_block = fixed_w_bytes_per_block(F, I, K)
     achieved = n * bytes_block / (ms / 1e3) / 1e9
     return {"value": n / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms, "fixed_from": K,
             "speedup_vs_fp32_w": plain_ms / ms, "psnr_db": ps(pf), "fp32_w_psnr_db": ps(plain_patches),
@@ -595,7 +604,7 @@ def main():
     frames = args.frames
     vid, mask, blocks = workload(rank, frames, dev)
     n_blocks = len(blocks)
-    eng = P.Engine([cls], device=local)
+    eng = P.Engine([cls], device=local, fixed_w=args.fixed_w)
     patches = torch.empty(n_blocks * 256, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -658,11 +667,11 @@ def main():
         peak_basis = f"derived: {sms} SMs x 128 B/clk x {sm_mhz:.0f} MHz (the measurement failed)"
 
     learned = curve = None
-    if not args.no_learned and args.iters == 200:
+    if not args.no_learned and args.iters == 200 and not args.fixed_w:
         learned = learned_leg(P, vid, mask, blocks, patches, args, stream, dev)
         curve = learned_curve(P, vid, mask, blocks, stream, dev)
     sweep = uneven = video = ordered = small = fixed = None
-    if not args.no_extra and args.iters == 200:
+    if not args.no_extra and args.iters == 200 and not args.fixed_w:
         fixed = fixed_w_leg(P, vid, mask, blocks, patches, ms, args, stream, dev, smem_peak)
         ordered = ordered_leg(P, vid, mask, blocks, patches, stream, dev)
         sweep = iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, smem_peak)
@@ -674,16 +683,19 @@ def main():
 
     # ---- roofline of the persistent kernel (shared-memory bound) ----
     F, I = cls["fft"], cls["iters"]
-    smem_bytes_block = smem_bytes_per_block(F, I)
+    smem_bytes_block = (fixed_w_bytes_per_block(F, I, P.FSE_FIXED_W_FROM) if args.fixed_w
+                        else smem_bytes_per_block(F, I))
     flops_block = I * F * F * 11.0 + 3 * 5.0 * F * F * np.log2(F * F)
     achieved = n_blocks * smem_bytes_block / (ms / 1e3) / 1e9
     peak = smem_peak
     fp32_peak = sms * 256.0 * sm_mhz * 1e6 / 1e12
-    traffic = profile_traffic()
+    traffic = None if args.fixed_w else profile_traffic()
     roofline = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "bytes_per_block": smem_bytes_block,
-                "bytes_basis": "8 I F^2 (one 8-byte W operand per bin and iteration) + 96 F^2 (the FFT passes, "
-                               "the weighting and the split: twelve 8-byte sweeps of the F x F grid)",
+                "bytes_basis": ("8 K F^2 + 4 (I - K) F^2 (8-byte FP32 W operands for the first K iterations, "
+                                "4-byte codes after) + 96 F^2" if args.fixed_w else
+                                "8 I F^2 (one 8-byte W operand per bin and iteration) + 96 F^2 (the FFT passes, "
+                                "the weighting and the split: twelve 8-byte sweeps of the F x F grid)"),
                 "peak_basis": peak_basis,
                 "fp32": {"achieved_tflops": n_blocks * flops_block / (ms / 1e3) / 1e12,
                          "peak_tflops": fp32_peak,
@@ -708,7 +720,9 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"{frames} x 3840x2160 u8 frames, 10% 16x16 losses per frame "
                                        f"({n_blocks} blocks per GPU), 48x48 areas, F=64, rho 0.8, "
-                                       f"gamma 0.5, I={I}, plain (zero) initialisation",
+                                       f"gamma 0.5, I={I}, plain (zero) initialisation"
+                                       + (f", 16-bit fixed-point W after {P.FSE_FIXED_W_FROM} FP32 updates"
+                                          if args.fixed_w else ""),
                            "parallelism": f"replicas x{world}", "blocks_per_gpu": n_blocks,
                            "l2": f"inputs larger than L2 (frames + mask = {2 * frames * H * W / 1e6:.0f} MB per GPU, "
                                  "L2 129 MB)"},

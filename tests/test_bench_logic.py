@@ -36,3 +36,12 @@ def test_shared_memory_bytes_per_block():
     assert bench.smem_bytes_per_block(64, 200) == 8 * 200 * 4096 + 96 * 4096
     assert bench.smem_bytes_per_block(64, 200) == pytest.approx(6.95e6, rel=1e-3)
     assert bench.smem_bytes_per_block(32, 0) == 96 * 1024
+
+
+
+def test_fixed_w_bytes_per_block():
+    """Reduced-precision storage: 8-byte operands for the first K iterations,
+    4-byte codes for the other I - K; the FP32 count when K >= I."""
+    assert bench.fixed_w_bytes_per_block(64, 200, 20) == (8 * 20 + 4 * 180) * 4096 + 96 * 4096
+    for I in (0, 1, 20):
+        assert bench.fixed_w_bytes_per_block(64, I, 20) == bench.smem_bytes_per_block(64, I)
