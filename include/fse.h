@@ -222,8 +222,10 @@ fse_status fse_load_init_weights(fse_handle *h, const float *params, size_t n);
  * patches (layout as above) back, and synchronises the stream before it
  * returns.  `patches` is a host FP32 array of sum_i b_i^2 values.
  * With two or more images (zero initialisation, no trace, not ordered) the
- * call is a pipeline: the block list is cut into up to 3 contiguous chunks
- * (1/16, 14/16 and 1/16 of a large batch), the images are uploaded in order
+ * call is a pipeline: the block list is cut into up to 8 contiguous chunks
+ * (1, 2, 4, 4, 4, 4, 4 and 1 parts of 24 of a large batch: each upload after
+ * the first is at most twice the work of the launch it overlaps), the images
+ * are uploaded in order
  * on a second stream while the chunks whose images (and, for video volumes,
  * neighbouring frames) are resident are concealed on `cuda_stream`, and each
  * chunk's patches are read back on a third stream once its launch ends.

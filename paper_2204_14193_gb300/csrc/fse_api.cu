@@ -37,7 +37,7 @@ namespace {
 thread_local std::string g_create_error = "no error";
 
 // chunks of the pipelined host-buffer path (upload / conceal / read back)
-constexpr int kHostChunks = 3;
+constexpr int kHostChunks = 8;
 
 struct DeviceGuard {  // restores the caller's current device
     int prev = -1;
@@ -889,10 +889,14 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
 // chunk's patches are read back on a third stream as soon as its launch ends.
 // A chunk is a contiguous range of the caller's block list and needs the
 // images up to the last one its blocks read (the frames +-(T-1)/2 around a
-// video volume's frame), so with blocks listed in image order the first
-// launch starts after 1/16 of the upload and only 1/16 of the patches are
-// read back after the last launch; in any other order the pipeline is still
-// correct, with less overlap.  Every block
+// video volume's frame).  With blocks listed in image order the chunk sizes
+// grow geometrically (1, 2, 4, 4, 4, 4, 4, 1 parts of 24): the first launch
+// starts after 1/24 of the upload, each later chunk's upload is at most twice
+// the previous chunk's work, so it stays hidden behind that launch unless the
+// host-to-device copy is slower than twice the rate at which the kernel
+// consumes frames, and only 1/24 of the patches are read back after the
+// last launch; in any other order the pipeline is still correct, with less
+// overlap.  Every block
 // is concealed by the same code from the same inputs as in the one-launch
 // path, so the patches are identical bit for bit.  The caller has validated
 // the batch (image, class and position of every block).
@@ -919,11 +923,12 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
     // chunk c: blocks [cs[c], cs[c+1]), patches [po[c], po[c+1]), images [0, need[c]) resident
     int cs[kHostChunks + 1], need[kHostChunks];
     long long po[kHostChunks + 1];
-    // a full pipeline has small first and last chunks (1/16 of the blocks
-    // each: the GPU waits for the first upload, the host for the last
-    // read-back) and one large chunk between; small batches: equal chunks
-    static const int kWeight[kHostChunks] = {1, 14, 1};
-    const bool weighted = K == kHostChunks && n_blocks >= 16 * 64;
+    // a full pipeline has small first and last chunks (the GPU waits for the
+    // first upload, the host for the last read-back) and chunks between that
+    // at most double, so every upload after the first overlaps the launch
+    // before it; small batches: equal chunks
+    static const int kWeight[kHostChunks] = {1, 2, 4, 4, 4, 4, 4, 1};
+    const bool weighted = K == kHostChunks && n_blocks >= 24 * 64;
     int wsum = 0, wacc = 0;
     for (int c = 0; c < K; ++c) wsum += weighted ? kWeight[c] : 1;
     for (int c = 0; c <= K; ++c) {

@@ -141,3 +141,47 @@ def test_fixw_trace_gap_is_unsupported(fse):
         assert ei.value.status == 2
     finally:
         eng.close()
+
+
+def test_fixw_warm_start_parity(fse):
+    """Warm start (fse_extrapolate_batch_init: the model starts from the
+    residual of caller estimates) with the fixed-point spectrum."""
+    img = synth.make_image(31, 256, 256)[None]
+    blocks = synth.grid_losses(32, 256, 256, 16, 0.25, non_adjacent=True)
+    mask = synth.loss_mask(blocks, [16], 1, 256, 256)
+    est = synth.noisy_estimates(33, img, blocks, [C64])
+    eng = fse.Engine([C64], trace=True, fixed_w=True)
+    try:
+        n = eng.patch_total(blocks)
+        patches = torch.zeros(n, dtype=torch.float32, device="cuda")
+        eng.run_init(torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda(), blocks,
+                     torch.from_numpy(est).cuda(), patches=patches)
+        torch.cuda.synchronize()
+        sel, energy = eng.trace()[:2]
+    finally:
+        eng.close()
+    res = parity.check_batch(img, mask, blocks, [C64], patches.cpu().numpy(), sel, energy, ests=est,
+                             wfix_from=fse.FSE_FIXED_W_FROM)
+    s = parity.summarize(res)
+    print("fixed-point warm start parity:", s)
+    assert s["ok"], s
+    parity.assert_strict_bounds(s, max_wide=MAX_WIDE_FIX)
+    assert s["exact_pix"] <= parity.PIX_TOL, s
+
+
+def test_fixw_host_pipeline_equals_device_path(fse):
+    """The host-buffer pipeline (several chunks) runs the same kernel set:
+    bit-identical patches to the device entry point."""
+    T, H, W = 6, 256, 320
+    video = synth.make_video(41, T, H, W)
+    blocks = np.concatenate([synth.grid_losses(42 + t, H, W, 16, 0.2, image=t) for t in range(T)])
+    mask = synth.loss_mask(blocks, [16], T, H, W)
+    cls = [dict(C64, iters=60)]
+    dev, _, _ = run(fse, cls, video, mask, blocks, trace=False)
+    eng = fse.Engine(cls, fixed_w=True)
+    try:
+        out = np.full(eng.patch_total(blocks), -1.0, np.float32)
+        eng.run_host(video, mask, blocks, out)
+    finally:
+        eng.close()
+    np.testing.assert_array_equal(out, dev)
