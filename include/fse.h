@@ -178,8 +178,9 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg);
  * persistent, graph-captured launch; the graph is rebuilt only when the block
  * list or a pointer changes.  The launch shape (threads per CTA, CTAs per SM)
  * is chosen by timing the candidates on the batch itself the first time a
- * class mix of that size appears in the process: that first call waits for
- * its timing runs; later calls and other handles reuse the choice.
+ * class mix of that size appears in the process; by default that first call
+ * waits for its timing runs (see fse_set_tuning for a mode that never waits);
+ * later calls and other handles reuse the choice.
  */
 fse_status fse_extrapolate_batch(fse_handle *h, const void *images, int dtype, int n_images,
                                  int height, int width, size_t pitch_bytes,
@@ -293,6 +294,30 @@ fse_status fse_sync(fse_handle *h);
  * exercise the timeout path.  Takes effect from the next call (a captured
  * launch is re-captured).  No counterpart in the paper. */
 fse_status fse_set_wait_limit(fse_handle *h, unsigned long long ns);
+
+/* How the handle chooses the launch shape (threads per CTA: 128 or 256, CTAs
+ * per SM: the two largest counts) of a class mix it has not seen (no
+ * counterpart in the paper).  Every shape gives the same outputs bit for
+ * bit; only the speed differs.
+ *   FSE_TUNE_SYNC  (default) the first call with the mix times the four
+ *                  shapes on the batch itself (two launches each) and waits
+ *                  for them before it enqueues its own launch;
+ *   FSE_TUNE_ASYNC no call waits: each call with an untuned mix runs its own
+ *                  launch with the next untimed shape, bracketed by events
+ *                  that later calls poll without blocking; once all four
+ *                  are timed the fastest is kept (so the first four or five
+ *                  calls run at the candidates' speeds, and re-plan instead
+ *                  of replaying a captured launch);
+ *   FSE_TUNE_OFF   128 threads per CTA at the largest CTA count, untimed.
+ * Measured choices (SYNC, ASYNC) go to the process-wide cache that other
+ * handles read; choices the handle already holds are kept.
+ * fse_get_tuning reports the mode and how many class mixes are still being
+ * timed asynchronously (either pointer may be NULL). */
+#define FSE_TUNE_SYNC 0
+#define FSE_TUNE_ASYNC 1
+#define FSE_TUNE_OFF 2
+fse_status fse_set_tuning(fse_handle *h, int mode);
+fse_status fse_get_tuning(const fse_handle *h, int *mode, int *pending);
 
 /* ------------------------------------------------------------------------
  * Learned initialisation network (no counterpart in the paper).
@@ -409,6 +434,9 @@ fse_status fse_measure_smem_bandwidth(int device, double *gbytes_per_s);
  * library holds now (handles, networks, staging), to check for leaks. */
 void fse_test_fail_allocation(int n);
 long long fse_test_live_allocations(void);
+/* Forgets the process-wide tuning cache (every handle's own choices stay),
+ * so a test can watch a class mix being tuned again. */
+void fse_test_clear_tuning_cache(void);
 
 /* Reason for the last failure on h (or, when h is NULL, of fse_create or
  * fse_extrapolate_batch_noalloc); never NULL; valid until the next call. */

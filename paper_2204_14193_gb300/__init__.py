@@ -84,6 +84,10 @@ def _load():
             lib.fse_get_area_model.argtypes = [vp, vp, sz, vp]
             lib.fse_sync.argtypes = [vp]
             lib.fse_set_wait_limit.argtypes = [vp, ctypes.c_ulonglong]
+            lib.fse_set_tuning.argtypes = [vp, c_int]
+            lib.fse_get_tuning.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+            lib.fse_test_clear_tuning_cache.argtypes = []
+            lib.fse_test_clear_tuning_cache.restype = None
             lib.fse_extrapolate_batch_noalloc.argtypes = [ctypes.POINTER(fse_class), c_int, vp, c_int, c_int,
                                                           c_int, c_int, sz, vp, vp, c_int, vp, vp]
             lib.fse_get_trace.argtypes = [vp, vp, vp, vp, sz, ctypes.POINTER(c_int)]
@@ -101,7 +105,7 @@ def _load():
             for n in ("fse_create", "fse_extrapolate_batch", "fse_extrapolate_batch_host",
                       "fse_extrapolate_batch_noalloc", "fse_get_trace", "fse_extrapolate_batch_init",
                       "fse_load_init_weights", "fse_get_area_model", "fse_sync", "fse_set_wait_limit",
-                      "fse_get_trace_gap"):
+                      "fse_get_trace_gap", "fse_set_tuning", "fse_get_tuning"):
                 getattr(lib, n).restype = c_int
             fp = ctypes.POINTER(ctypes.c_float)
             lib.fse_cnn_param_count.restype = sz
@@ -241,6 +245,25 @@ def fse_sync(h) -> None:
 
 def fse_set_wait_limit(h, ns: int) -> None:
     _check(_load().fse_set_wait_limit(h, int(ns)), h)
+
+
+FSE_TUNE_SYNC, FSE_TUNE_ASYNC, FSE_TUNE_OFF = 0, 1, 2
+TUNE_MODES = {"sync": FSE_TUNE_SYNC, "async": FSE_TUNE_ASYNC, "off": FSE_TUNE_OFF}
+
+
+def fse_set_tuning(h, mode: int) -> None:
+    _check(_load().fse_set_tuning(h, int(mode)), h)
+
+
+def fse_get_tuning(h):
+    """(mode, class mixes still being timed asynchronously)."""
+    m, p = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_load().fse_get_tuning(h, ctypes.byref(m), ctypes.byref(p)), h)
+    return m.value, p.value
+
+
+def fse_test_clear_tuning_cache() -> None:
+    _load().fse_test_clear_tuning_cache()
 
 
 def fse_measure_smem_bandwidth(device: int = 0) -> float:
@@ -495,6 +518,17 @@ class Engine:
     def set_wait_limit(self, ns: int):
         """Limit of the bounded device waits in nanoseconds (default 1 s)."""
         fse_set_wait_limit(self.h, ns)
+
+    def set_tuning(self, mode: str):
+        """How new class mixes choose their launch shape: "sync" (default:
+        the first call times the candidates and waits), "async" (no call
+        waits; candidates are timed on the real launches) or "off"."""
+        fse_set_tuning(self.h, TUNE_MODES[mode])
+
+    def tuning(self):
+        """(mode name, class mixes still being timed asynchronously)."""
+        m, p = fse_get_tuning(self.h)
+        return {v: k for k, v in TUNE_MODES.items()}[m], p
 
     def area_model(self, stream=None):
         """Re{g} over every block's M x M area of the last batch (trace

@@ -115,6 +115,18 @@ struct fse_handle {
     int ks = fse::kSetImage;       // kernel set of the captured launch
     // autotuner: chosen (threads per CTA, CTAs per SM) per class-mix signature
     std::vector<std::pair<uint64_t, std::pair<int, int>>> tuned;
+    int tune_mode = FSE_TUNE_SYNC;
+    // FSE_TUNE_ASYNC: candidates timed on the handle's real launches, one
+    // per call, until each class mix has a choice
+    struct TuneSession {
+        uint64_t tune_key = 0, mix_sig = 0;
+        int n = 0;
+        int nt[4] = {}, cps[4] = {};
+        cudaEvent_t e0[4] = {}, e1[4] = {};
+        int state[4] = {};     // 0 not launched, 1 launched (events recorded), 2 timed
+        float ms[4] = {};
+    };
+    std::vector<TuneSession> sessions;
     // host-buffer staging
     void *d_img = nullptr;
     size_t img_cap = 0;
@@ -601,13 +613,113 @@ fse_status capture_graph(fse_handle *h, int ks, int nt, int grid, cudaGraphExec_
 std::mutex g_tune_mu;
 std::unordered_map<uint64_t, std::pair<int, int>> g_tuned;
 
+// A launch the asynchronous autotuner times: the caller records e0 / e1 of
+// session `s` around it (s < 0: no timing).
+struct TuneTicket {
+    int s = -1, i = -1;
+};
+
+void destroy_session(fse_handle::TuneSession &ss) {
+    for (int i = 0; i < 4; ++i) {
+        if (ss.e0[i]) cudaEventDestroy(ss.e0[i]);
+        if (ss.e1[i]) cudaEventDestroy(ss.e1[i]);
+        ss.e0[i] = ss.e1[i] = nullptr;
+    }
+}
+
+void remember_choice(fse_handle *h, const Plan &pl, int nt, int cps, bool global) {
+    h->tuned.emplace_back(pl.mix_sig, std::make_pair(nt, cps));
+    if (global) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[pl.tune_key] = std::make_pair(nt, cps);
+    }
+}
+
+// FSE_TUNE_ASYNC: poll the session's timed launches without waiting; once
+// every candidate is timed, keep the fastest.  Otherwise hand out the next
+// untimed candidate with a ticket, or (all launched, some still running)
+// the fastest timed so far, else the first candidate.
+fse_status autotune_async(fse_handle *h, const Plan &pl, int *best_nt, int *best_cps, TuneTicket *t) {
+    int si = -1;
+    for (int k = 0; k < (int)h->sessions.size(); ++k)
+        if (h->sessions[k].tune_key == pl.tune_key && h->sessions[k].mix_sig == pl.mix_sig) si = k;
+    if (si < 0) {
+        fse_handle::TuneSession ss;
+        ss.tune_key = pl.tune_key;
+        ss.mix_sig = pl.mix_sig;
+        for (int nt : {128, 256}) {
+            const int maxc = ctas_per_sm(h, pl.ks, nt);
+            for (int cps = std::max(1, maxc - 1); cps <= maxc && ss.n < 4; ++cps) {
+                ss.nt[ss.n] = nt;
+                ss.cps[ss.n] = cps;
+                ++ss.n;
+            }
+        }
+        h->sessions.push_back(ss);
+        si = (int)h->sessions.size() - 1;
+    }
+    fse_handle::TuneSession &ss = h->sessions[si];
+    int timed = 0, best = -1;
+    for (int i = 0; i < ss.n; ++i) {
+        if (ss.state[i] == 1) {
+            const cudaError_t q = cudaEventQuery(ss.e1[i]);
+            if (q == cudaSuccess) {
+                FSE_CUDA(h, cudaEventElapsedTime(&ss.ms[i], ss.e0[i], ss.e1[i]));
+                ss.state[i] = 2;
+            } else if (q != cudaErrorNotReady) {
+                return cuda_fail(h, q, "autotune event");
+            }
+        }
+        if (ss.state[i] == 2) {
+            ++timed;
+            if (best < 0 || ss.ms[i] < ss.ms[best]) best = i;
+        }
+    }
+    if (timed == ss.n) {
+        *best_nt = ss.nt[best];
+        *best_cps = ss.cps[best];
+        remember_choice(h, pl, *best_nt, *best_cps, true);
+        destroy_session(ss);
+        h->sessions.erase(h->sessions.begin() + si);
+        return FSE_OK;
+    }
+    for (int i = 0; i < ss.n; ++i)
+        if (ss.state[i] == 0) {
+            if (!ss.e0[i]) FSE_CUDA(h, cudaEventCreate(&ss.e0[i]));
+            if (!ss.e1[i]) FSE_CUDA(h, cudaEventCreate(&ss.e1[i]));
+            *best_nt = ss.nt[i];
+            *best_cps = ss.cps[i];
+            t->s = si;
+            t->i = i;
+            return FSE_OK;
+        }
+    const int c = best >= 0 ? best : 0;
+    *best_nt = ss.nt[c];
+    *best_cps = ss.cps[c];
+    return FSE_OK;
+}
+
+// Records the ticket's start event (before the timed launch) or end event.
+fse_status tune_mark(fse_handle *h, const TuneTicket &t, cudaStream_t stream, bool end) {
+    if (t.s < 0) return FSE_OK;
+    fse_handle::TuneSession &ss = h->sessions[t.s];
+    FSE_CUDA(h, cudaEventRecord(end ? ss.e1[t.i] : ss.e0[t.i], stream));
+    if (end) ss.state[t.i] = 1;
+    return FSE_OK;
+}
+
 // Autotuner: time each candidate mapping -- 128 threads per CTA (32 bins per
 // thread) or 256 (16 bins per thread), the two largest CTA counts per SM --
 // on the actual batch (the outputs are identical for every candidate, so the
 // runs are harmless) and keep the fastest per class mix, in the handle and
-// in the process-wide cache.  The first call with a new class mix waits for
-// its timing runs; later calls (and other handles) reuse the choice.
-fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *best_nt, int *best_cps) {
+// in the process-wide cache.  FSE_TUNE_SYNC: the first call with a new class
+// mix waits for its timing runs.  FSE_TUNE_ASYNC: no call waits; each call
+// times one candidate on its own launch (ticket *t) until all are timed.
+// FSE_TUNE_OFF: 128 threads per CTA at the largest CTA count (the measured
+// choice for the FFT-64 classes), untimed.  Later calls (and, for measured
+// choices, other handles) reuse the choice.
+fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *best_nt, int *best_cps,
+                    TuneTicket *t = nullptr) {
     for (auto &kv : h->tuned)
         if (kv.first == pl.mix_sig) {
             *best_nt = kv.second.first;
@@ -625,6 +737,14 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
         }
     }
     int bnt = 256, bcps = ctas_per_sm(h, pl.ks, 256);
+    if (h->tune_mode == FSE_TUNE_OFF) {
+        *best_nt = 128;
+        *best_cps = ctas_per_sm(h, pl.ks, 128);
+        remember_choice(h, pl, *best_nt, *best_cps, false);
+        return FSE_OK;
+    }
+    if (h->tune_mode == FSE_TUNE_ASYNC && t && (long long)pl.total_items >= 2LL * h->sm_count)
+        return autotune_async(h, pl, best_nt, best_cps, t);
     // small batches cannot fill the machine: no measurement needed
     if ((long long)pl.total_items >= 2LL * h->sm_count) {
         cudaEvent_t e0, e1;
@@ -657,11 +777,7 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    h->tuned.emplace_back(pl.mix_sig, std::make_pair(bnt, bcps));
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[pl.tune_key] = std::make_pair(bnt, bcps);
-    }
+    remember_choice(h, pl, bnt, bcps, true);
     *best_nt = bnt;
     *best_cps = bcps;
     return FSE_OK;
@@ -870,7 +986,8 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
         h->ordered_n = n_blocks;
     }
     int nt = 256, cps = ctas_per_sm(h, pl.ks, 256);
-    st = autotune(h, pl, stream, &nt, &cps);
+    TuneTicket ticket;
+    st = autotune(h, pl, stream, &nt, &cps, &ticket);
     if (st != FSE_OK) return st;
     h->nt = nt;
     h->ks = pl.ks;
@@ -878,9 +995,15 @@ fse_status run_batch(fse_handle *h, const void *images, int dtype, int n_images,
     st = capture_graph(h, pl.ks, nt, h->grid, &h->gexec);
     if (st != FSE_OK) return st;
     h->graph_valid = true;
-    h->plan_key = key;
+    // while this class mix is still being tuned (FSE_TUNE_ASYNC), the next
+    // call plans again instead of replaying this launch's configuration
+    bool tuning = false;
+    for (const auto &ss : h->sessions) tuning = tuning || ss.mix_sig == pl.mix_sig;
+    h->plan_key = tuning ? 0 : key;
+    st = tune_mark(h, ticket, stream, false);
+    if (st != FSE_OK) return st;
     FSE_CUDA(h, cudaGraphLaunch(h->gexec, stream));
-    return FSE_OK;
+    return tune_mark(h, ticket, stream, true);
 }
 
 // Host-buffer batches over several images run as a pipeline of up to
@@ -1031,16 +1154,21 @@ fse_status run_host_chunked(fse_handle *h, const void *images, int dtype, int n_
         setup_tma(h, P, pc.ks, dtype, h->d_img, h->d_mask, n_images, height, width, pitch);
         PIPE_CUDA(cudaStreamWaitEvent(stream, h->ev_in[c], 0));
         int nt = 256, cps = ctas_per_sm(h, pc.ks, 256);
+        TuneTicket ticket;
         {   // the autotuner times graph replays of h->params: lend it this chunk's
             const DevParams saved = h->params;
             h->params = P;
-            st = autotune(h, pc, stream, &nt, &cps);
+            st = autotune(h, pc, stream, &nt, &cps, &ticket);
             h->params = saved;
             if (st != FSE_OK) return drain(st);
         }
         const int grid = std::max(1, std::min(pc.total_items, cps * h->sm_count));
         PIPE_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(int), stream));
+        st = tune_mark(h, ticket, stream, false);
+        if (st != FSE_OK) return drain(st);
         PIPE_CUDA(launch_fse(h, pc.ks, nt, grid, P, stream));
+        st = tune_mark(h, ticket, stream, true);
+        if (st != FSE_OK) return drain(st);
         PIPE_CUDA(cudaEventRecord(h->ev_k[c], stream));
     }
     // read-backs after every launch is queued (a copy to pageable memory
@@ -1358,6 +1486,26 @@ fse_status fse_set_wait_limit(fse_handle *h, unsigned long long ns) {
     return FSE_OK;
 }
 
+fse_status fse_set_tuning(fse_handle *h, int mode) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (mode != FSE_TUNE_SYNC && mode != FSE_TUNE_ASYNC && mode != FSE_TUNE_OFF)
+        return fail(h, FSE_ERR_INVALID_ARG, "tuning mode %d unknown", mode);
+    h->tune_mode = mode;
+    return FSE_OK;
+}
+
+fse_status fse_get_tuning(const fse_handle *h, int *mode, int *pending) {
+    if (!h) return fail(nullptr, FSE_ERR_INVALID_ARG, "handle is NULL");
+    if (mode) *mode = h->tune_mode;
+    if (pending) *pending = (int)h->sessions.size();
+    return FSE_OK;
+}
+
+void fse_test_clear_tuning_cache(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+}
+
 const char *fse_last_error(const fse_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 void fse_destroy(fse_handle *h) {
@@ -1399,6 +1547,7 @@ void fse_destroy(fse_handle *h) {
             if (h->ev_in[c]) cudaEventDestroy(h->ev_in[c]);
             if (h->ev_k[c]) cudaEventDestroy(h->ev_k[c]);
         }
+        for (auto &ss : h->sessions) destroy_session(ss);
         if (h->ev_start) cudaEventDestroy(h->ev_start);
         if (h->ev_out) cudaEventDestroy(h->ev_out);
         if (h->h2d_stream) cudaStreamDestroy(h->h2d_stream);

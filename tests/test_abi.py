@@ -111,3 +111,13 @@ def test_fixed_w_config_validation(kw, status):
     hdr = open(HEADER).read()
     assert re.search(r"#define FSE_FLAG_FIXED_W (\d+)u", hdr).group(1) == str(P.FSE_FLAG_FIXED_W)
     assert re.search(r"#define FSE_FIXED_W_FROM (\d+)", hdr).group(1) == str(P.FSE_FIXED_W_FROM)
+
+
+def test_tuning_api_argument_errors():
+    lib = P._load()
+    assert lib.fse_set_tuning(None, 0) == 1
+    assert lib.fse_get_tuning(None, None, None) == 1
+    assert (P.FSE_TUNE_SYNC, P.FSE_TUNE_ASYNC, P.FSE_TUNE_OFF) == (0, 1, 2)
+    hdr = open(HEADER).read()
+    for name, v in (("FSE_TUNE_SYNC", 0), ("FSE_TUNE_ASYNC", 1), ("FSE_TUNE_OFF", 2)):
+        assert re.search(rf"#define {name} (\d+)", hdr).group(1) == str(v)
