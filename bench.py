@@ -432,7 +432,7 @@ def iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, peak_gbs):
     return out
 
 
-def uneven_batch(P, args, stream, dev, with_oracle=False, seconds=6.0):
+def uneven_batch(P, args, stream, dev, peak_gbs, with_oracle=False, seconds=6.0):
     """30 frames of 1920x1080 u8 video, 3% of the samples lost in mixed
     4x4 / 8x8 / 16x16 blocks (borders 6/12/16, FFT 16/32/64), I = 200, one
     launch over all sizes."""
@@ -464,10 +464,13 @@ def uneven_batch(P, args, stream, dev, with_oracle=False, seconds=6.0):
         rate, nd = oracle_rate(jobs, seconds, cores)
         oracle_line = {"value": rate, "unit": "blocks/s", "threads": cores, "blocks_done": nd, "kind": "oracle",
                        "sample": "seeded sample of the batch's blocks (all three sizes)"}
+    # shared-memory roofline: each class's algorithmic bytes per block
+    nbytes = sum(int(counts[c]) * smem_bytes_per_block(k["fft"], k["iters"]) for c, k in enumerate(classes))
     return {"value": len(blocks) / (ms / 1e3), "unit": "blocks/s", "ms_per_step": ms, "oracle": oracle_line,
             "workload": f"{T3} x {W3}x{H3} u8 frames, 3% of samples lost in 4/8/16 blocks "
                         f"({counts[0]}/{counts[1]}/{counts[2]}), F 16/32/64, I=200, one launch",
-            "blocks": int(len(blocks))}
+            "blocks": int(len(blocks)), "smem_bytes_per_launch": nbytes,
+            "smem_frac": nbytes / (ms / 1e3) / 1e9 / peak_gbs}
 
 
 def video_volumes(P, args, stream, dev, peak_gbs):
@@ -695,7 +698,7 @@ def main():
         fixed = fixed_w_leg(P, vid, mask, blocks, patches, ms, args, stream, dev, smem_peak)
         ordered = ordered_leg(P, vid, mask, blocks, patches, stream, dev)
         sweep = iteration_sweep(P, vid, mask, blocks, patches, args, stream, dev, smem_peak)
-        uneven = uneven_batch(P, args, stream, dev, with_oracle=rank == 0 and not args.no_cpu_baseline,
+        uneven = uneven_batch(P, args, stream, dev, smem_peak, with_oracle=rank == 0 and not args.no_cpu_baseline,
                               seconds=args.cpu_seconds / 2)
         video = video_volumes(P, args, stream, dev, smem_peak)
         small = small_configs(P, stream, dev, with_oracle=rank == 0 and not args.no_cpu_baseline,

@@ -185,3 +185,41 @@ def test_fixw_host_pipeline_equals_device_path(fse):
     finally:
         eng.close()
     np.testing.assert_array_equal(out, dev)
+
+
+def test_fixw_full_size_sampled(fse):
+    """The benchmark's headline launch (64 x 3840x2160 u8 frames, 10% 16x16
+    losses, F=64, I=200) with FSE_FLAG_FIXED_W: bit-identical with and
+    without the trace, and 48 sampled blocks meet both bars."""
+    T, H, W = 64, 2160, 3840
+    vid = synth.make_video_torch(21, T, H, W, device="cuda")
+    blocks = np.concatenate([synth.grid_losses(1000 + t, H, W, 16, 0.10, image=t) for t in range(T)])
+    mask_np = synth.loss_mask(blocks, [16], T, H, W)
+    dmask = torch.from_numpy(mask_np).cuda()
+    n = len(blocks)
+    res = {}
+    for trace in (False, True):
+        eng = fse.Engine([C64], trace=trace, fixed_w=True)
+        patches = torch.zeros(n * 256, dtype=torch.float32, device="cuda")
+        eng.run(vid, dmask, blocks, patches=patches)
+        torch.cuda.synchronize()
+        res[trace] = (patches.cpu().numpy(), eng.trace()[:2] if trace else None)
+        eng.close()
+    np.testing.assert_array_equal(res[False][0], res[True][0])
+    rng = np.random.default_rng(6)
+    pick = np.sort(rng.choice(n, 48, replace=False))
+    host = {f: vid[f].cpu().numpy() for f in sorted(set(int(blocks[i, 0]) for i in pick))}
+    sel, energy = res[True][1]
+    out = []
+    for i in pick:
+        bk = blocks[i].copy()
+        f = int(bk[0])
+        bk[0] = 0
+        p = res[True][0][256 * i:256 * (i + 1)].reshape(16, 16).astype(np.float64)
+        out.append(parity.check_block(host[f], mask_np[f], bk, [C64], p, sel[i], energy[i],
+                                      wfix_from=fse.FSE_FIXED_W_FROM))
+    s = parity.summarize(out)
+    print("fixed-point full-size sample:", s)
+    assert s["ok"], s
+    parity.assert_strict_bounds(s, max_wide=MAX_WIDE_FIX)
+    assert s["exact_pix"] <= parity.PIX_TOL, s
