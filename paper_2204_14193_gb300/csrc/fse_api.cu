@@ -628,6 +628,16 @@ void destroy_session(fse_handle::TuneSession &ss) {
 }
 
 void remember_choice(fse_handle *h, const Plan &pl, int nt, int cps, bool global) {
+    // a choice closes any asynchronous session of the mix (one left open when
+    // the mode changed): its launches no longer decide anything, and an open
+    // session keeps the mix from replaying its captured graph
+    for (size_t k = 0; k < h->sessions.size();)
+        if (h->sessions[k].tune_key == pl.tune_key && h->sessions[k].mix_sig == pl.mix_sig) {
+            destroy_session(h->sessions[k]);
+            h->sessions.erase(h->sessions.begin() + k);
+        } else {
+            ++k;
+        }
     h->tuned.emplace_back(pl.mix_sig, std::make_pair(nt, cps));
     if (global) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -678,9 +688,7 @@ fse_status autotune_async(fse_handle *h, const Plan &pl, int *best_nt, int *best
     if (timed == ss.n) {
         *best_nt = ss.nt[best];
         *best_cps = ss.cps[best];
-        remember_choice(h, pl, *best_nt, *best_cps, true);
-        destroy_session(ss);
-        h->sessions.erase(h->sessions.begin() + si);
+        remember_choice(h, pl, *best_nt, *best_cps, true);   // closes the session
         return FSE_OK;
     }
     for (int i = 0; i < ss.n; ++i)
@@ -730,11 +738,15 @@ fse_status autotune(fse_handle *h, const Plan &pl, cudaStream_t stream, int *bes
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(pl.tune_key);
         if (it != g_tuned.end()) {
-            h->tuned.emplace_back(pl.mix_sig, it->second);
             *best_nt = it->second.first;
             *best_cps = it->second.second;
-            return FSE_OK;
+        } else {
+            *best_nt = 0;
         }
+    }
+    if (*best_nt > 0) {   // measured by another handle (or an earlier one)
+        remember_choice(h, pl, *best_nt, *best_cps, false);
+        return FSE_OK;
     }
     int bnt = 256, bcps = ctas_per_sm(h, pl.ks, 256);
     if (h->tune_mode == FSE_TUNE_OFF) {

@@ -100,3 +100,29 @@ def test_tuning_off_and_host_pipeline(P, batch):
         ref.close()
         off.close()
         asy.close()
+
+
+def test_switching_mode_closes_an_open_session(P, batch):
+    """An ASYNC session left open when the handle switches to SYNC is closed
+    by the synchronous choice (the mix then replays its captured launch)."""
+    video, mask, blocks = batch
+    P.fse_test_clear_tuning_cache()
+    eng = P.Engine([CLS])
+    try:
+        eng.set_tuning("async")
+        dv, dm = torch.from_numpy(video).cuda(), torch.from_numpy(mask).cuda()
+        n = eng.patch_total(blocks)
+        a = torch.zeros(n, device="cuda")
+        eng.run(dv, dm, blocks, patches=a)
+        assert eng.tuning() == ("async", 1)
+        eng.set_tuning("sync")
+        b = torch.zeros(n, device="cuda")
+        eng.run(dv, dm, blocks, patches=b)
+        assert eng.tuning() == ("sync", 0)
+        c = torch.zeros(n, device="cuda")
+        eng.run(dv, dm, blocks, patches=c)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+        np.testing.assert_array_equal(a.cpu().numpy(), c.cpu().numpy())
+    finally:
+        eng.close()
