@@ -898,6 +898,10 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     const bool gap = GAP && P.tr_second != nullptr;
     if (iters > 0) pick = group_argmax<F, PAIRS, NT, 1, GAP>(Rre, Rim, tmax, jb, gr, rsh, 0, gap);
 
+    // Two copies of the iteration loop: the kernel sets without reduced-
+    // precision storage keep the single loop below (the two-phase form, even
+    // with its second phase compiled out, changed their register allocation
+    // and spills); kSetFixW runs the two-phase form after it.
     if constexpr (!FIXW) {
         const ulonglong2 *Wq = reinterpret_cast<const ulonglong2 *>(region);
         for (int nu = 1; nu <= iters; ++nu) {
