@@ -1255,7 +1255,7 @@ fse_status fse_create(fse_handle **out, const fse_config *cfg) {
     size_t smem = 0;
     for (int c = 0; c < cfg->n_classes; ++c) {
         const int F = cfg->cls[c].fft;
-        smem = std::max(smem, (size_t)fse::cta_region_bytes(F));
+        smem = std::max(smem, (size_t)fse::cta_region_bytes(F, cfg->cls[c].frames > 1 ? 4 : 1));
     }
     h->smem_bytes = smem;
     h->ext = (cfg->flags & FSE_FLAG_ORDERED) != 0;

@@ -241,14 +241,28 @@ struct Geo {
     static constexpr int RSTEP = TB / LPR;           // row groups of the block's threads
     // F = 64: a thread's rows are runs of 8 consecutive rows, and W carries a
     // copy of rows 0..6 after row F-1, so a shifted run never wraps (its 8
-    // loads address one base with immediate offsets).  Other sizes: rows
-    // r0, r0 + RSTEP, ... and one select per load at the wrap.
+    // loads address one base with immediate offsets).  Volumes of F = 32
+    // (VRUNS): in every temporal plane a thread's rows are a run of KPR
+    // consecutive rows, and each plane of W carries a copy of its rows 0..2
+    // after its row F-1 (PROWS rows per plane), so each plane's KPR loads
+    // address one base with immediate offsets.  Other sizes: rows r0, r0 +
+    // RSTEP, ... and one select (images) or one register offset (volumes)
+    // per load.
     static constexpr bool RUNS = F == 64 && FT == 1;
-    static constexpr int WROWS = RUNS ? F + 7 : F;   // W chunk rows in shared memory
-    static constexpr int REGION = RUNS ? 16 * F * WROWS : 16 * F * F * FT;   // smem bytes per block
+    static constexpr bool VRUNS = F == 32 && FT == 4;
+    static constexpr int KPR = F / RSTEP > 0 ? F / RSTEP : 1;   // a thread's rows per plane (volumes)
+    static constexpr int WROWS = RUNS ? F + 7 : F;   // W chunk rows in shared memory (images)
+    static constexpr int PROWS = VRUNS ? F + 3 : F;  // W chunk rows per plane (volumes)
+    static constexpr int REGION = RUNS ? 16 * F * WROWS : 16 * F * PROWS * FT;   // smem bytes per block
     __device__ __forceinline__ static int row(int r0, int i) {   // spectrum row of pair i
         if constexpr (RUNS) return (((i >> 3) * RSTEP + r0) << 3) + (i & 7);
+        else if constexpr (VRUNS) return (i / KPR) * F + KPR * r0 + i % KPR;
         else return r0 + i * RSTEP;
+    }
+    // W chunk row in shared memory of spectrum row k (plane k / F)
+    __device__ __forceinline__ static int wrow(int k) {
+        if constexpr (VRUNS) return (k / F) * PROWS + k % F;
+        else return k;
     }
     static constexpr int FP = F + 1;                 // padded row of the FFT buffer
     static constexpr int R1 = (F == 16) ? 4 : 8;     // four-step FFT radices
@@ -259,14 +273,19 @@ struct Geo {
     static_assert(RSTEP * PAIRS == FT * F, "thread rows must tile the spectrum");
     static_assert(FT == 1 || F % RSTEP == 0, "a thread's rows repeat in every temporal plane");
     static_assert(!RUNS || PAIRS % 8 == 0, "runs of 8 rows");
+    static_assert(!VRUNS || (KPR * RSTEP == F && KPR * FT == PAIRS && KPR - 1 <= PROWS - F),
+                  "volume runs tile every plane and the copied rows cover a shifted run");
     static_assert(REGION >= 8 * FT * F * FP, "the FFT buffer fits the region");
     static_assert(!RUNS || (kTmaStage >= 8 * F * FP && kTmaStage + kTmaStageMax <= REGION),
                   "the TMA staging area lies between the FFT buffer and the end of the region");
 };
 
 // dynamic shared memory of one CTA working on blocks of FFT size F (one
-// F = 64 block, or 4096 / F^2 smaller blocks)
-__host__ __device__ constexpr int cta_region_bytes(int F) { return F == 64 ? 16 * 64 * (64 + 7) : 65536; }
+// F = 64 block, or 4096 / F^2 smaller blocks) or on volumes (FT = 4: one F =
+// 32 volume with its copied rows, or four F = 16 volumes)
+__host__ __device__ constexpr int cta_region_bytes(int F, int FT = 1) {
+    return F == 64 ? 16 * 64 * (64 + 7) : (F == 32 && FT == 4) ? 16 * 32 * (32 + 3) * 4 : 65536;
+}
 
 constexpr int kMaxWarps = 8;
 
@@ -1243,23 +1262,24 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         Rre[i] = pk(R2[0].x, R2[1].x);
         Rim[i] = pk(R2[0].y, R2[1].y);
         Wc[i] = make_float4(W2[0].x, W2[1].x, W2[0].y, W2[1].y);
-        if (k >= SAFE) {
-            Wd[k * F + c0] = Wc[i];
-            Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        const int kw = G::wrow(k);
+        if (kw >= SAFE) {
+            Wd[kw * F + c0] = Wc[i];
+            Wd[kw * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     const float W00 = Z[0].y * ainv;
     gsync<F, PAIRS, NT, FT>(gr);
 #pragma unroll
     for (int i = 0; i < PAIRS; ++i) {
-        const int k = G::row(r0, i);
-        if (k < SAFE) {
-            Wd[k * F + c0] = Wc[i];
-            Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        const int k = G::row(r0, i), kw = G::wrow(k);
+        if (kw < SAFE) {
+            Wd[kw * F + c0] = Wc[i];
+            Wd[kw * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
-        if (G::RUNS && k < G::WROWS - F) {   // the copy of the first rows after row F-1
-            Wd[(k + F) * F + c0] = Wc[i];
-            Wd[(k + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+        if (G::VRUNS && k % F < G::PROWS - F) {   // each plane's copy of its first rows after row F-1
+            Wd[(kw + F) * F + c0] = Wc[i];
+            Wd[(kw + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     gsync<F, PAIRS, NT, FT>(gr);
@@ -1342,12 +1362,23 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         // Volumes: pair i lies in plane i / KP at row r0 + (i % KP) RSTEP; its
         // shifted chunk is plane (i / KP - wt) mod FT, row (r0 + (i % KP) RSTEP
         // - u) mod F: KP row offsets and FT plane offsets per iteration.
+        // Volume runs (VRUNS): pair i lies in plane i / KP at row KP r0 +
+        // i % KP; the shifted rows of one plane are consecutive from (KP r0 -
+        // u) mod F (the plane's copied rows absorb the wrap): one base per
+        // plane, immediate offsets.
         constexpr int KP = FT == 1 ? 1 : F / RSTEP;
         int kofs[KP], tofs[FT];
+        const ulonglong2 *Pb[FT];
+        if constexpr (G::VRUNS) {
+            const int rbase = ((KP * r0 - u) & (F - 1)) * F + qcol;
 #pragma unroll
-        for (int j2 = 0; j2 < KP; ++j2) kofs[j2] = ((r0 + j2 * RSTEP - u) & (F - 1)) * F + qcol;
+            for (int p2 = 0; p2 < FT; ++p2) Pb[p2] = Wq + ((p2 - wt) & (FT - 1)) * G::PROWS * F + rbase;
+        } else {
 #pragma unroll
-        for (int p2 = 0; p2 < FT; ++p2) tofs[p2] = ((p2 - wt) & (FT - 1)) * F * F;
+            for (int j2 = 0; j2 < KP; ++j2) kofs[j2] = ((r0 + j2 * RSTEP - u) & (F - 1)) * F + qcol;
+#pragma unroll
+            for (int p2 = 0; p2 < FT; ++p2) tofs[p2] = ((p2 - wt) & (FT - 1)) * F * F;
+        }
         tmax = 0.f;
 #pragma unroll
         for (int j = 0; j < NQ; ++j) {
@@ -1356,7 +1387,8 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
             for (int ii = 0; ii < 4; ++ii) {
                 const int i = 4 * j + ii;
                 // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                const ulonglong2 w = FT > 1    ? Wq[tofs[i / KP] + kofs[i % KP]]
+                const ulonglong2 w = G::VRUNS ? Pb[G::VRUNS ? i / KP : 0][(i % KP) * F]
+                                     : FT > 1  ? Wq[tofs[i / KP] + kofs[i % KP]]
                                      : G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
                                                : (i < iw ? A : A2)[i * RSTEP * F];
                 const uint64_t wre = w.x, wim = w.y;

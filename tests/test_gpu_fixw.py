@@ -223,3 +223,40 @@ def test_fixw_full_size_sampled(fse):
     assert s["ok"], s
     parity.assert_strict_bounds(s, max_wide=MAX_WIDE_FIX)
     assert s["exact_pix"] <= parity.PIX_TOL, s
+
+
+def test_fixw_after_learned_initialisation(fse):
+    """The learned pipeline with reduced-precision storage: the network's
+    estimate on B (taken from the same handle configuration with zero
+    iterations) starts the fixed-point iterations, which meet both bars."""
+    from paper_2204_14193_gb300 import train_init as T
+    w = T.load_weights()
+    img = synth.make_image(51, 384, 384)[None]
+    blocks = synth.grid_losses(52, 384, 384, 16, 0.2, non_adjacent=True)
+    mask = synth.loss_mask(blocks, [16], 1, 384, 384)
+    dimg, dmask = torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda()
+    n = len(blocks)
+    est_b = torch.zeros(n * 256, device="cuda")
+    e0 = fse.Engine([dict(C64, iters=0)], init="learned", init_iters=0, weights=w, fixed_w=True)
+    e0.run(dimg, dmask, blocks, patches=est_b)
+    e0.close()
+    eng = fse.Engine([C64], trace=True, init="learned", init_iters=60, weights=w, fixed_w=True)
+    out = torch.zeros(n * 256, device="cuda")
+    eng.run(dimg, dmask, blocks, patches=out)
+    eng.sync()
+    torch.cuda.synchronize()
+    sel, energy = eng.trace()[:2]
+    eng.close()
+    est = np.zeros((n, 48 * 48))
+    eb = est_b.cpu().numpy().reshape(n, 16, 16)
+    for i in range(n):
+        a = np.zeros((48, 48))
+        a[16:32, 16:32] = eb[i]
+        est[i] = a.ravel()
+    res = parity.check_batch(img, mask, blocks, [C64], out.cpu().numpy(), sel, energy, ests=est, iters=60,
+                             wfix_from=fse.FSE_FIXED_W_FROM)
+    s = parity.summarize(res)
+    print("fixed-point after learned initialisation:", s)
+    assert s["ok"], s
+    parity.assert_strict_bounds(s, max_wide=MAX_WIDE_FIX)
+    assert s["exact_pix"] <= parity.PIX_TOL, s
