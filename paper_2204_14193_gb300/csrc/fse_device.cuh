@@ -239,24 +239,30 @@ struct Geo {
     static constexpr int TB = FT * F * F / (2 * PAIRS);   // threads per block
     static constexpr int LPR = F / 2;                // lanes per spectrum row
     static constexpr int RSTEP = TB / LPR;           // row groups of the block's threads
-    // F = 64: a thread's rows are runs of 8 consecutive rows, and W carries a
-    // copy of rows 0..6 after row F-1, so a shifted run never wraps (its 8
-    // loads address one base with immediate offsets).  Volumes of F = 32
+    // F = 64 (F = 32): a thread's rows are runs of RL = 8 (4) consecutive
+    // rows, and W carries a copy of rows 0..RL-2 after row F-1, so a shifted
+    // run never wraps (its RL loads address one base with immediate
+    // offsets).  Volumes of F = 32
     // (VRUNS): in every temporal plane a thread's rows are a run of KPR
     // consecutive rows, and each plane of W carries a copy of its rows 0..2
     // after its row F-1 (PROWS rows per plane), so each plane's KPR loads
     // address one base with immediate offsets.  Other sizes: rows r0, r0 +
     // RSTEP, ... and one select (images) or one register offset (volumes)
     // per load.
-    static constexpr bool RUNS = F == 64 && FT == 1;
+    static constexpr bool RUNS = (F == 64 || F == 32) && FT == 1;
+    static constexpr int RL = F == 64 ? 8 : 4;       // rows per run (images)
+    static constexpr int RLS = F == 64 ? 3 : 2;      // log2(RL)
     static constexpr bool VRUNS = F == 32 && FT == 4;
     static constexpr int KPR = F / RSTEP > 0 ? F / RSTEP : 1;   // a thread's rows per plane (volumes)
-    static constexpr int WROWS = RUNS ? F + 7 : F;   // W chunk rows in shared memory (images)
+    static constexpr int KPS = KPR >= 4 ? 2 : KPR == 2 ? 1 : 0;   // log2(KPR) for the volume runs
+    static constexpr int WROWS = RUNS ? F + RL - 1 : F;   // W chunk rows in shared memory (images)
     static constexpr int PROWS = VRUNS ? F + 3 : F;  // W chunk rows per plane (volumes)
     static constexpr int REGION = RUNS ? 16 * F * WROWS : 16 * F * PROWS * FT;   // smem bytes per block
     __device__ __forceinline__ static int row(int r0, int i) {   // spectrum row of pair i
-        if constexpr (RUNS) return (((i >> 3) * RSTEP + r0) << 3) + (i & 7);
-        else if constexpr (VRUNS) return (i / KPR) * F + KPR * r0 + i % KPR;
+        // (shifts: i may be a run-time slot index, whose sign the compiler
+        // cannot see)
+        if constexpr (RUNS) return (((i >> RLS) * RSTEP + r0) << RLS) + (i & (RL - 1));
+        else if constexpr (VRUNS) return (i >> KPS) * F + (r0 << KPS) + (i & (KPR - 1));
         else return r0 + i * RSTEP;
     }
     // W chunk row in shared memory of spectrum row k (plane k / F)
@@ -272,11 +278,12 @@ struct Geo {
     static constexpr int NQ = PAIRS / 4;                 // quartets of pairs
     static_assert(RSTEP * PAIRS == FT * F, "thread rows must tile the spectrum");
     static_assert(FT == 1 || F % RSTEP == 0, "a thread's rows repeat in every temporal plane");
-    static_assert(!RUNS || PAIRS % 8 == 0, "runs of 8 rows");
-    static_assert(!VRUNS || (KPR * RSTEP == F && KPR * FT == PAIRS && KPR - 1 <= PROWS - F),
+    static_assert(!RUNS || PAIRS % RL == 0, "a thread's rows are whole runs");
+    static_assert(!RUNS || RL == (1 << RLS), "runs of a power-of-two length");
+    static_assert(!VRUNS || (KPR == (1 << KPS) && KPR * RSTEP == F && KPR * FT == PAIRS && KPR - 1 <= PROWS - F),
                   "volume runs tile every plane and the copied rows cover a shifted run");
     static_assert(REGION >= 8 * FT * F * FP, "the FFT buffer fits the region");
-    static_assert(!RUNS || (kTmaStage >= 8 * F * FP && kTmaStage + kTmaStageMax <= REGION),
+    static_assert(F != 64 || (kTmaStage >= 8 * F * FP && kTmaStage + kTmaStageMax <= REGION),
                   "the TMA staging area lies between the FFT buffer and the end of the region");
 };
 
@@ -284,7 +291,8 @@ struct Geo {
 // F = 64 block, or 4096 / F^2 smaller blocks) or on volumes (FT = 4: one F =
 // 32 volume with its copied rows, or four F = 16 volumes)
 __host__ __device__ constexpr int cta_region_bytes(int F, int FT = 1) {
-    return F == 64 ? 16 * 64 * (64 + 7) : (F == 32 && FT == 4) ? 16 * 32 * (32 + 3) * 4 : 65536;
+    // F = 32: four blocks (or one volume) of 35 W chunk rows per plane
+    return F == 64 ? 16 * 64 * (64 + 7) : F == 32 ? 16 * 32 * (32 + 3) * 4 : 65536;
 }
 
 constexpr int kMaxWarps = 8;
@@ -699,7 +707,7 @@ template <int F, int PAIRS, int NT, int NP, bool EXT = false, bool GAP = false, 
 __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, int first, int count,
                                         unsigned char *smem, const float2 *s_tw, RedShared *rsh, uint32_t &tph) {
     using G = Geo<F, PAIRS>;
-    static_assert(!FIXW || G::RUNS, "the fixed-point spectrum uses the F = 64 chunk rows");
+    static_assert(!FIXW || (G::RUNS && F == 64), "the fixed-point spectrum uses the F = 64 chunk rows");
     constexpr bool TRW = GAP || FIXW;   // trace writes compiled in
     constexpr int TB = G::TB, LPR = G::LPR, RSTEP = G::RSTEP, FP = G::FP, NQ = G::NQ;
     Grp gr;
@@ -743,7 +751,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     constexpr int NPOS = F * F / TB;
     float sv[NPOS];
     uint8_t mk[NPOS];
-    if (TMA && G::RUNS && P.tma) {
+    if (TMA && F == 64 && P.tma) {
         // 8-bit F = 64 windows: the image and mask tiles of the M x M area
         // arrive in shared memory by two TMA copies.  The tile's first column
         // is the area's first column rounded down to a 16-byte boundary (xs
@@ -953,17 +961,17 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
             // at pair iw.  Pairs before the wrap address from A, the others from
             // A - F*F, so each load needs one select and an immediate offset.
-            // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
-            // contiguous in W (rows F.. repeat rows 0..6): one base per run.
+            // Runs: run j starts at row (row(r0, RL j) - u) mod F and its RL rows are
+            // contiguous in W (rows F.. repeat rows 0..RL-2): one base per run.
             const int qcol = (c0 - v) & (F - 1);
             const int rb = (r0 - u) & (F - 1);
             const int iw = (F - rb + RSTEP - 1) / RSTEP;
             const ulonglong2 *A = Wq + rb * F + qcol;
             const ulonglong2 *A2 = A - F * F;
-            const ulonglong2 *Ar[G::RUNS ? PAIRS / 8 : 1];
+            const ulonglong2 *Ar[G::RUNS ? PAIRS / G::RL : 1];
     #pragma unroll
-            for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
-                Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+            for (int r = 0; r < (G::RUNS ? PAIRS / G::RL : 1); ++r)
+                Ar[r] = Wq + ((G::row(r0, G::RL * r) - u) & (F - 1)) * F + qcol;
             tmax = 0.f;
     #pragma unroll
             for (int j = 0; j < NQ; ++j) {
@@ -972,7 +980,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
                 for (int ii = 0; ii < 4; ++ii) {
                     const int i = 4 * j + ii;
                     // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                    const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                    const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i / G::RL : 0][(i % G::RL) * F]
                                                  : (i < iw ? A : A2)[i * RSTEP * F];
                     const uint64_t wre = w.x, wim = w.y;
                     uint64_t a = fma2(ncr, wre, Rre[i]);
@@ -1031,8 +1039,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
             // at pair iw.  Pairs before the wrap address from A, the others from
             // A - F*F, so each load needs one select and an immediate offset.
-            // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
-            // contiguous in W (rows F.. repeat rows 0..6): one base per run.
+            // Runs: run j starts at row (row(r0, RL j) - u) mod F and its RL rows are
+            // contiguous in W (rows F.. repeat rows 0..RL-2): one base per run.
             using Chunk = typename std::conditional<FX, uint2, ulonglong2>::type;
             const Chunk *Wq = reinterpret_cast<const Chunk *>(region);
             const int qcol = (c0 - v) & (F - 1);
@@ -1040,10 +1048,10 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             const int iw = (F - rb + RSTEP - 1) / RSTEP;
             const Chunk *A = Wq + rb * F + qcol;
             const Chunk *A2 = A - F * F;
-            const Chunk *Ar[G::RUNS ? PAIRS / 8 : 1];
+            const Chunk *Ar[G::RUNS ? PAIRS / G::RL : 1];
     #pragma unroll
-            for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
-                Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+            for (int r = 0; r < (G::RUNS ? PAIRS / G::RL : 1); ++r)
+                Ar[r] = Wq + ((G::row(r0, G::RL * r) - u) & (F - 1)) * F + qcol;
             tmax = 0.f;
     #pragma unroll
             for (int j = 0; j < NQ; ++j) {
@@ -1053,7 +1061,7 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
                     const int i = 4 * j + ii;
                     // one load: (Re W, Re W') and (Im W, Im W') as two f32x2
                     // operands (16 bytes of FP32, or 8 bytes of codes)
-                    const Chunk w = G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                    const Chunk w = G::RUNS ? Ar[G::RUNS ? i / G::RL : 0][(i % G::RL) * F]
                                             : (i < iw ? A : A2)[i * RSTEP * F];
                     uint64_t wre, wim;
                     if constexpr (FX) {
@@ -1348,17 +1356,17 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         // Non-runs: the row of pair i is (r0 - u + i*RSTEP) mod F; it wraps once,
         // at pair iw.  Pairs before the wrap address from A, the others from
         // A - F*F, so each load needs one select and an immediate offset.
-        // Runs: run j starts at row (row(r0, 8j) - u) mod F and its 8 rows are
-        // contiguous in W (rows F.. repeat rows 0..6): one base per run.
+        // Runs: run j starts at row (row(r0, RL j) - u) mod F and its RL rows are
+        // contiguous in W (rows F.. repeat rows 0..RL-2): one base per run.
         const int qcol = (c0 - v) & (F - 1);
         const int rb = (r0 - u) & (F - 1);
         const int iw = (F - rb + RSTEP - 1) / RSTEP;
         const ulonglong2 *A = Wq + rb * F + qcol;
         const ulonglong2 *A2 = A - F * F;
-        const ulonglong2 *Ar[G::RUNS ? PAIRS / 8 : 1];
+        const ulonglong2 *Ar[G::RUNS ? PAIRS / G::RL : 1];
 #pragma unroll
-        for (int r = 0; r < (G::RUNS ? PAIRS / 8 : 1); ++r)
-            Ar[r] = Wq + ((G::row(r0, 8 * r) - u) & (F - 1)) * F + qcol;
+        for (int r = 0; r < (G::RUNS ? PAIRS / G::RL : 1); ++r)
+            Ar[r] = Wq + ((G::row(r0, G::RL * r) - u) & (F - 1)) * F + qcol;
         // Volumes: pair i lies in plane i / KP at row r0 + (i % KP) RSTEP; its
         // shifted chunk is plane (i / KP - wt) mod FT, row (r0 + (i % KP) RSTEP
         // - u) mod F: KP row offsets and FT plane offsets per iteration.
@@ -1389,7 +1397,7 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
                 // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
                 const ulonglong2 w = G::VRUNS ? Pb[G::VRUNS ? i / KP : 0][(i % KP) * F]
                                      : FT > 1  ? Wq[tofs[i / KP] + kofs[i % KP]]
-                                     : G::RUNS ? Ar[G::RUNS ? i >> 3 : 0][(i & 7) * F]
+                                     : G::RUNS ? Ar[G::RUNS ? i / G::RL : 0][(i % G::RL) * F]
                                                : (i < iw ? A : A2)[i * RSTEP * F];
                 const uint64_t wre = w.x, wim = w.y;
                 uint64_t a = fma2(ncr, wre, Rre[i]);
