@@ -285,7 +285,16 @@ fse_status fse_get_area_model(fse_handle *h, float *model, size_t model_stride, 
  *   FSE_ERR_INVALID_ARG  a block's loss area B is not marked lost in the
  *                        loss mask (the blocks must be lost samples); that
  *                        block was concealed as if B were lost.
- * The handle stays usable after either. */
+ *   FSE_ERR_CUDA         (bounds-checked library only) an index into a
+ *                        shared-memory spectrum, the output image or the
+ *                        block list left its buffer; the kernel skipped the
+ *                        access (or the block) and carried on.
+ * The handle stays usable after any of them.
+ * The library is also built bounds-checked (libfse_checked.so, compiled with
+ * FSE_BOUNDS_CHECK; the Python binding loads it when the environment sets
+ * FSE_BOUNDS_CHECK=1): same interface and results, with the kernels' W-chunk
+ * loads and stores, output stores and block descriptors checked against
+ * their buffers.  It stands in for a memory checker where none can run. */
 fse_status fse_sync(fse_handle *h);
 
 /* Limit of every bounded device wait of the handle's launches, in

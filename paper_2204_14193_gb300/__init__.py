@@ -62,7 +62,9 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: libfse.so, or the bounds-checked
+    libfse_checked.so when the environment sets FSE_BOUNDS_CHECK=1."""
+    return _build.LIB_CHECKED if os.environ.get("FSE_BOUNDS_CHECK") == "1" else _build.LIB
 
 
 def _load():
@@ -71,7 +73,7 @@ def _load():
         if _lib is None:
             if _build.needs_build():
                 _build.build_library()
-            lib = ctypes.CDLL(_build.LIB)
+            lib = ctypes.CDLL(library_path())
             vp, c_int, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
             lib.fse_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(fse_config)]
             lib.fse_extrapolate_batch.argtypes = [vp, vp, c_int, c_int, c_int, c_int, sz, vp, vp, c_int,

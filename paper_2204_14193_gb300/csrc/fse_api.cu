@@ -1477,6 +1477,8 @@ fse_status fse_sync(fse_handle *h) {
     FSE_CUDA(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e != 0) {
         FSE_CUDA(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        if (e & fse::kErrBounds)
+            return fail(h, FSE_ERR_CUDA, "device bounds check: an index left its buffer (access skipped)");
         if (e & fse::kErrTimeout)
             return fail(h, FSE_ERR_TIMEOUT, "a bounded device wait ran out (limit %llu ns)", h->wait_ns);
         return fail(h, FSE_ERR_INVALID_ARG, "a lost block's loss area is not marked lost in the loss mask");

@@ -103,6 +103,7 @@ struct DevParams {
 // bits of the device status word (read and cleared by fse_sync)
 constexpr int kErrTimeout = 1;    // a bounded wait ran out
 constexpr int kErrUnmarked = 2;   // a block's loss area B is not marked lost in the mask
+constexpr int kErrBounds = 4;     // (bounds-checked builds) an index left its buffer; the access was skipped
 // after an expired wait the kernel still waits this long, at most, for its
 // own asynchronous copies in flight
 constexpr unsigned long long kDrainNs = 1000000000ull;
@@ -110,6 +111,26 @@ constexpr unsigned long long kDrainNs = 1000000000ull;
 __device__ __forceinline__ void report(const DevParams &P, int bit) {
     if (P.err != nullptr) atomicOr(P.err, bit);
 }
+
+#ifdef FSE_BOUNDS_CHECK
+// Bounds-checked builds (-DFSE_BOUNDS_CHECK, libfse_checked.so): index i of a
+// buffer of n elements.  Outside [0, n) it is recorded in the status word
+// (kErrBounds, reported by fse_sync) and 0 is used instead, so the access
+// stays inside the buffer and the kernel runs on.  Other builds compile the
+// unchecked expressions.
+__device__ __forceinline__ long long bchk(const DevParams &P, long long i, long long n) {
+    if (i < 0 || i >= n) {
+        report(P, kErrBounds);
+        return 0;
+    }
+    return i;
+}
+#define FSE_IX(i, n) bchk(P, (i), (n))
+#define FSE_LD(base, ptr, n) (base)[bchk(P, (ptr) - (base), (n))]
+#else
+#define FSE_IX(i, n) (i)
+#define FSE_LD(base, ptr, n) (*(ptr))
+#endif
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -719,6 +740,15 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     const int lt = gr.lt;
 
     const BlockRec blk = P.blocks[first + gr.g];
+#ifdef FSE_BOUNDS_CHECK
+    // the block lies inside its image (the host validates this too); the
+    // whole group skips a block that does not
+    if (blk.image < 0 || blk.image >= P.n_images || blk.x < 0 || blk.y < 0 || blk.x + C.b > P.W ||
+        blk.y + C.b > P.H) {
+        report(P, kErrBounds);
+        return;
+    }
+#endif
     unsigned char *region = smem + gr.g * G::REGION;
     float2 *Z = reinterpret_cast<float2 *>(region);
 
@@ -875,8 +905,8 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
         Rim[i] = pk(R2[0].y, R2[1].y);
         Wc[i] = make_float4(W2[0].x, W2[1].x, W2[0].y, W2[1].y);
         if (k >= SAFE) {
-            Wd[k * F + c0] = Wc[i];
-            Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+            Wd[FSE_IX(k * F + c0, G::REGION / 16)] = Wc[i];
+            Wd[FSE_IX(k * F + c0 + F / 2, G::REGION / 16)] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     const float W00 = Z[0].y * ainv;
@@ -885,12 +915,12 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
     for (int i = 0; i < PAIRS; ++i) {
         const int k = G::row(r0, i);
         if (k < SAFE) {
-            Wd[k * F + c0] = Wc[i];
-            Wd[k * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+            Wd[FSE_IX(k * F + c0, G::REGION / 16)] = Wc[i];
+            Wd[FSE_IX(k * F + c0 + F / 2, G::REGION / 16)] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
         if (G::RUNS && k < G::WROWS - F) {   // the copy of the first rows after row F-1
-            Wd[(k + F) * F + c0] = Wc[i];
-            Wd[(k + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+            Wd[FSE_IX((k + F) * F + c0, G::REGION / 16)] = Wc[i];
+            Wd[FSE_IX((k + F) * F + c0 + F / 2, G::REGION / 16)] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     gsync<F, PAIRS, NT>(gr);
@@ -980,8 +1010,9 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
                 for (int ii = 0; ii < 4; ++ii) {
                     const int i = 4 * j + ii;
                     // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                    const ulonglong2 w = G::RUNS ? Ar[G::RUNS ? i / G::RL : 0][(i % G::RL) * F]
-                                                 : (i < iw ? A : A2)[i * RSTEP * F];
+                    const ulonglong2 w =
+                        G::RUNS ? FSE_LD(Wq, Ar[G::RUNS ? i / G::RL : 0] + (i % G::RL) * F, G::REGION / 16)
+                                : FSE_LD(Wq, (i < iw ? A : A2) + i * RSTEP * F, G::REGION / 16);
                     const uint64_t wre = w.x, wim = w.y;
                     uint64_t a = fma2(ncr, wre, Rre[i]);
                     Rre[i] = fma2(pci, wim, a);
@@ -1061,8 +1092,9 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
                     const int i = 4 * j + ii;
                     // one load: (Re W, Re W') and (Im W, Im W') as two f32x2
                     // operands (16 bytes of FP32, or 8 bytes of codes)
-                    const Chunk w = G::RUNS ? Ar[G::RUNS ? i / G::RL : 0][(i % G::RL) * F]
-                                            : (i < iw ? A : A2)[i * RSTEP * F];
+                    const Chunk w =
+                        G::RUNS ? FSE_LD(Wq, Ar[G::RUNS ? i / G::RL : 0] + (i % G::RL) * F, G::WROWS * F)
+                                : FSE_LD(Wq, (i < iw ? A : A2) + i * RSTEP * F, G::WROWS * F);
                     uint64_t wre, wim;
                     if constexpr (FX) {
                         wre = fix_unpack(w.x, nbias2);
@@ -1112,7 +1144,9 @@ __device__ __forceinline__ void process(const DevParams &P, const DevClass &C, i
             const int pm = j / b, pn = j % b;
             float val = acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
             if (P.clamp_u8) val = rintf(fminf(fmaxf(val, 0.f), 255.f));
-            if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
+            if (P.out != nullptr)
+                P.out[FSE_IX(((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn,
+                             (long long)P.n_images * P.H * P.W)] = val;
             if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
         }
     }
@@ -1146,6 +1180,15 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     const int lt = gr.lt;
 
     const BlockRec blk = P.blocks[first + gr.g];
+#ifdef FSE_BOUNDS_CHECK
+    // the block lies inside its image (the host validates this too); the
+    // whole group skips a block that does not
+    if (blk.image < 0 || blk.image >= P.n_images || blk.x < 0 || blk.y < 0 || blk.x + C.b > P.W ||
+        blk.y + C.b > P.H) {
+        report(P, kErrBounds);
+        return;
+    }
+#endif
     unsigned char *region = smem + gr.g * G::REGION;
     float2 *Z = reinterpret_cast<float2 *>(region);
 
@@ -1272,8 +1315,8 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
         Wc[i] = make_float4(W2[0].x, W2[1].x, W2[0].y, W2[1].y);
         const int kw = G::wrow(k);
         if (kw >= SAFE) {
-            Wd[kw * F + c0] = Wc[i];
-            Wd[kw * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+            Wd[FSE_IX(kw * F + c0, G::REGION / 16)] = Wc[i];
+            Wd[FSE_IX(kw * F + c0 + F / 2, G::REGION / 16)] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     const float W00 = Z[0].y * ainv;
@@ -1282,12 +1325,12 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
     for (int i = 0; i < PAIRS; ++i) {
         const int k = G::row(r0, i), kw = G::wrow(k);
         if (kw < SAFE) {
-            Wd[kw * F + c0] = Wc[i];
-            Wd[kw * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+            Wd[FSE_IX(kw * F + c0, G::REGION / 16)] = Wc[i];
+            Wd[FSE_IX(kw * F + c0 + F / 2, G::REGION / 16)] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
         if (G::VRUNS && k % F < G::PROWS - F) {   // each plane's copy of its first rows after row F-1
-            Wd[(kw + F) * F + c0] = Wc[i];
-            Wd[(kw + F) * F + c0 + F / 2] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
+            Wd[FSE_IX((kw + F) * F + c0, G::REGION / 16)] = Wc[i];
+            Wd[FSE_IX((kw + F) * F + c0 + F / 2, G::REGION / 16)] = make_float4(Wc[i].y, Wc[i].x, Wc[i].w, Wc[i].z);
         }
     }
     gsync<F, PAIRS, NT, FT>(gr);
@@ -1395,10 +1438,11 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
             for (int ii = 0; ii < 4; ++ii) {
                 const int i = 4 * j + ii;
                 // one 16-byte load: (Re W, Re W') and (Im W, Im W') as two f32x2 operands
-                const ulonglong2 w = G::VRUNS ? Pb[G::VRUNS ? i / KP : 0][(i % KP) * F]
-                                     : FT > 1  ? Wq[tofs[i / KP] + kofs[i % KP]]
-                                     : G::RUNS ? Ar[G::RUNS ? i / G::RL : 0][(i % G::RL) * F]
-                                               : (i < iw ? A : A2)[i * RSTEP * F];
+                const ulonglong2 w =
+                    G::VRUNS ? FSE_LD(Wq, Pb[G::VRUNS ? i / KP : 0] + (i % KP) * F, G::REGION / 16)
+                    : FT > 1 ? FSE_LD(Wq, Wq + tofs[i / KP] + kofs[i % KP], G::REGION / 16)
+                    : G::RUNS ? FSE_LD(Wq, Ar[G::RUNS ? i / G::RL : 0] + (i % G::RL) * F, G::REGION / 16)
+                              : FSE_LD(Wq, (i < iw ? A : A2) + i * RSTEP * F, G::REGION / 16);
                 const uint64_t wre = w.x, wim = w.y;
                 uint64_t a = fma2(ncr, wre, Rre[i]);
                 Rre[i] = fma2(pci, wim, a);
@@ -1425,7 +1469,9 @@ __device__ __forceinline__ void process_vol(const DevParams &P, const DevClass &
             const int pm = j / b, pn = j % b;
             float val = acc[t] + (P.est != nullptr ? P.est[blk.orig * P.est_stride + (d + pm) * M + d + pn] : 0.f);
             if (P.clamp_u8) val = rintf(fminf(fmaxf(val, 0.f), 255.f));
-            if (P.out != nullptr) P.out[((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn] = val;
+            if (P.out != nullptr)
+                P.out[FSE_IX(((size_t)blk.image * P.H + blk.y + pm) * P.W + blk.x + pn,
+                             (long long)P.n_images * P.H * P.W)] = val;
             if (P.patches != nullptr) P.patches[blk.patch_off + j] = val;
         }
     }

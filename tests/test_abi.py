@@ -29,6 +29,15 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def test_checked_library_exports_every_declared_symbol():
+    """The bounds-checked build (FSE_BOUNDS_CHECK) offers the same interface."""
+    from paper_2204_14193_gb300 import _build
+    P._load()   # builds both libraries if needed
+    lib = ctypes.CDLL(_build.LIB_CHECKED)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
 def test_ctypes_structs_match_header_layout():
     prog = r'''
 #include <stdio.h>
