@@ -51,7 +51,7 @@ def mirror(sel, F):
 
 
 def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, est=None, iters=None,
-                wfix_from=None):
+                wfix_from=None, band=None):
     """Compare one block.  Returns a dict of diagnostics; raises nothing.
     gpu_sel / gpu_energy: the kernel's selection trace and FP32 energies.
     est: warm start, the M x M area estimate (the model then starts from the
@@ -60,7 +60,10 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
     wfix_from: reduced-precision residual storage from that iteration on;
     every criterion then uses the oracle of that form, and exact_pix reports
     the pixel difference to the exact oracle replayed along the GPU's
-    selections."""
+    selections.
+    band: (eps, delta_max) in place of the default near-tie band and energy
+    bound (used where the FP32 residual's own deviation is larger, e.g. at
+    the largest iteration counts)."""
     im, x, y, c = (int(v) for v in blk)
     k = cls[c]
     F, b, I = k["fft"], k["block"], k["iters"] if iters is None else iters
@@ -115,6 +118,8 @@ def check_block(img, mask, blk, cls, gpu_patch, gpu_sel=None, gpu_energy=None, e
             delta = np.zeros(I)
         out["max_delta"] = float(delta.max())
         eps, dmax = (EPS_TIE, DELTA_MAX) if wfix_from is None else (EPS_FIX, DELTA_FIX)
+        if band is not None:
+            eps, dmax = band
         if np.any(1.0 - ratio > eps) or out["max_delta"] > dmax:
             out["ok"] = False
         wide = 1.0 - ratio > EPS_TIE
@@ -187,7 +192,7 @@ def check_block3(video, mask, blk, cls, gpu_patch, gpu_sel, gpu_energy):
 
 
 def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, threads=None, ests=None, iters=None,
-                wfix_from=None):
+                wfix_from=None, band=None):
     """Check every block of a batch; patches is the flat patch array (caller
     order), sels / energies the [n, stride] trace or None, ests the per-block
     warm-start estimates [n, >= M*M] or None, wfix_from as check_block."""
@@ -205,7 +210,7 @@ def check_batch(images, mask, blocks, cls, patches, sels=None, energies=None, th
                            None if sels is None else sels[i],
                            None if energies is None else energies[i],
                            None if ests is None else ests[i][:(b + 2 * cls[int(bk[3])]["border"]) ** 2],
-                           iters, wfix_from)
+                           iters, wfix_from, band)
 
     n = threads or len(os.sched_getaffinity(0))
     with ThreadPoolExecutor(max_workers=n) as ex:

@@ -348,3 +348,24 @@ def test_no_support_gives_zero_model(fse):
     eng.sync()
     eng.close()
     assert np.all(out.cpu().numpy() == 77.25)
+
+
+def test_maximum_iteration_count(fse):
+    """I = 4096, the largest count the boundary accepts.  After thousands of
+    updates the FP32 residual's energies deviate from FP64 by up to about
+    1e-3 (measured 1.06e-3 at I = 4096, against under 2e-4 up to I = 500),
+    more than the gaps of some near-ties, so the strict 1e-5 band does not
+    hold there (18 of 32,768 picks fell outside it, worst 1.7e-4).  Every
+    pick is still an argmax of the kernel's own residual, hence a
+    (1 - 2 delta)-argmax of the FP64 one: the test bounds delta by 3e-3 and
+    the picks by 2 x 3e-3, and keeps the 1e-2 pixel bar (measured 1.2e-3)."""
+    img = synth.make_image(61, 128, 128)[None]
+    blocks = synth.grid_losses(62, 128, 128, 16, 0.2, non_adjacent=True)[:8]
+    mask = synth.loss_mask(blocks, [16], 1, 128, 128)
+    cls = [dict(C64, iters=4096)]
+    patches, sel, _ = run_gpu(fse, cls, img, mask, blocks)
+    res = parity.check_batch(img, mask, blocks, cls, patches, sel[0], sel[1], band=(6e-3, 3e-3))
+    s = parity.summarize(res)
+    print("I = 4096:", s)
+    assert s["ok"], s
+    assert s["worst_pix"] <= parity.PIX_TOL
